@@ -1,0 +1,183 @@
+"""Checks that pin the oracle to something other than itself.
+
+Each check is independent of ``oracle/cx_oracle.cpp``:
+
+* ``rotation_bwt`` - the textbook BWT by sorting rotations (Burrows & Wheeler
+  1994) of the concatenation S_0 $_0 S_1 $_1 ... S_{n-1} $_{n-1} over an
+  integer alphabet in which $_i = i and the bases follow as n..n+3.  Because
+  every end marker is a distinct symbol, comparing two rotations always stops at
+  or before the first marker, which is exactly the order of Section 2.  Python
+  list comparison does the sorting; nothing is shared with the oracle's
+  comparator.
+* worked examples (Figure 1) and hand-derived cases under ``tests/golden/``.
+* closed forms: one read is the plain BWT of S$; n identical reads repeat each
+  symbol of that BWT n times.
+* invariants at any size: symbol counts equal the input composition plus n $;
+  the first n symbols are the last bases of reads 0..n-1; LF-mapping inversion
+  (Ferragina & Manzini 2000) started at row i recovers read i exactly and ends
+  at that read's $ row.
+
+The same invariants double as the full-size property checks of the GPU path.
+"""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+SYMS = "$ACGT"
+
+
+def rotation_bwt(reads):
+    """BWT of a collection by brute-force rotation sorting (integer alphabet)."""
+    n = len(reads)
+    T = []
+    owner = []
+    for i, r in enumerate(reads):
+        T.extend(n + "ACGT".index(c) for c in r)
+        T.append(i)  # $_i
+    total = len(T)
+    rots = sorted(range(total), key=lambda p: T[p:] + T[:p])
+    out = []
+    for p in rots:
+        prev = T[p - 1]  # cyclic: T[-1] is $_{n-1}
+        out.append("$" if prev < n else "ACGT"[prev - n])
+    return "".join(out)
+
+
+def read_figure1():
+    with open(os.path.join(GOLDEN, "figure1.txt")) as f:
+        rows = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    d = {r[0]: r[1:] for r in rows}
+    return d["reads"], d["sorted_suffixes"], d["bwt"][0]
+
+
+def read_hand_examples():
+    out = []
+    with open(os.path.join(GOLDEN, "hand_examples.txt")) as f:
+        for ln in f:
+            ln = ln.strip()
+            if not ln or ln.startswith("#"):
+                continue
+            reads, want = (x.strip() for x in ln.split("->"))
+            out.append((reads.split(","), want))
+    return out
+
+
+def lf_invert(bwt: bytes, n: int, max_len: int):
+    """Recover every read from the BWT by LF-mapping.
+
+    Returns ``(reads_reversed, end_rows)``: for each read i, its bases in
+    reverse order as a list of uint8 arrays of codes, and the row at which the
+    walk met $.  Raises if a walk does not meet $ within ``max_len + 1`` steps.
+    """
+    B = np.frombuffer(bwt, dtype=np.uint8)
+    lut = np.full(256, 255, dtype=np.uint8)
+    for s, ch in enumerate(SYMS):
+        lut[ord(ch)] = s
+    sym = lut[B]
+    if np.any(sym == 255):
+        raise ValueError("BWT holds a symbol outside $ACGT")
+    N = sym.size
+    cnt = np.bincount(sym, minlength=5).astype(np.int64)
+    C = np.concatenate([[0], np.cumsum(cnt)[:-1]])
+    occ = np.empty(N, dtype=np.int64)
+    for s in range(5):
+        m = sym == s
+        occ[m] = np.arange(int(cnt[s]), dtype=np.int64)
+    LF = C[sym] + occ
+    rows = np.arange(n, dtype=np.int64)
+    active = np.ones(n, dtype=bool)
+    collected = []
+    end_rows = np.full(n, -1, dtype=np.int64)
+    for _ in range(max_len + 1):
+        s = sym[rows]
+        done = active & (s == 0)
+        end_rows[done] = rows[done]
+        active &= s != 0
+        if not active.any():
+            break
+        step = np.where(active, s.astype(np.int64) - 1, -1)
+        collected.append(step)
+        rows = np.where(active, LF[rows], rows)
+    if active.any():
+        raise AssertionError("LF walk did not reach $ for some read")
+    if collected:
+        M = np.stack(collected, axis=1)
+    else:
+        M = np.zeros((n, 0), dtype=np.int64)
+    reads_rev = [M[i][M[i] >= 0].astype(np.uint8) for i in range(n)]
+    return reads_rev, end_rows
+
+
+def check_invariants(codes: np.ndarray, lens: np.ndarray, bwt: bytes, dollar_pos=None, counts=None):
+    """Assert the size-independent properties of a multi-string BWT."""
+    codes = np.asarray(codes, dtype=np.uint8)
+    lens = np.asarray(lens, dtype=np.int64)
+    n = lens.size
+    N = int(lens.sum()) + n
+    assert len(bwt) == N, f"BWT length {len(bwt)} != {N}"
+    B = np.frombuffer(bwt, dtype=np.uint8)
+    want_counts = np.concatenate([[n], np.bincount(codes, minlength=4)]).astype(np.int64)
+    got_counts = np.array([np.count_nonzero(B == ord(c)) for c in SYMS], dtype=np.int64)
+    assert np.array_equal(got_counts, want_counts), f"counts {got_counts} != {want_counts}"
+    if counts is not None:
+        assert np.array_equal(np.asarray(counts, dtype=np.int64), want_counts)
+    # The n terminator-only suffixes are the n smallest, in read order; each is
+    # preceded by the last base of its read.
+    ends = np.cumsum(lens) - 1
+    last = np.frombuffer(b"ACGT", dtype=np.uint8)[codes[ends]]
+    assert np.array_equal(B[:n], last), "first n symbols are not the last bases of the reads"
+    rev, end_rows = lf_invert(bwt, n, int(lens.max()))
+    off = np.concatenate([[0], np.cumsum(lens)[:-1]])
+    for i in range(n):
+        want = codes[off[i]:off[i] + lens[i]][::-1]
+        if not np.array_equal(rev[i], want):
+            raise AssertionError(f"LF inversion of read {i} does not give the read back")
+    if dollar_pos is not None:
+        assert np.array_equal(np.asarray(dollar_pos, dtype=np.int64), end_rows), "dollar positions differ from LF walk"
+
+
+# ---------------------------------------------------------------------------
+# Whole pin suite against an oracle library (used by the mutant test, which
+# runs it in a subprocess against deliberately broken oracle builds).
+# ---------------------------------------------------------------------------
+
+def run_all_pins(lib=None, n_random=300, seed=7):
+    """Run every pin against an oracle library; returns the list of failed pin names."""
+    import oracle
+    from paper_1401_7457_gb300 import synth
+
+    failed = []
+
+    def bwt_of(reads):
+        return oracle.bwt(oracle.Collection.from_strings(reads), lib=lib)["bwt"].decode()
+
+    reads, _, want = read_figure1()
+    if bwt_of(reads) != want:
+        failed.append("figure1")
+    for reads, want in read_hand_examples():
+        if bwt_of(reads) != want:
+            failed.append("hand:" + ",".join(reads))
+            break
+    rng = np.random.default_rng(seed)
+    for _ in range(n_random):
+        k = int(rng.integers(1, 6))
+        alpha = "ACGT"[: int(rng.integers(1, 5))]
+        reads = ["".join(rng.choice(list(alpha), size=int(rng.integers(1, 9)))) for _ in range(k)]
+        if bwt_of(reads) != rotation_bwt(reads):
+            failed.append("brute_force")
+            break
+    base = "GATTACAGATTACA"
+    one = bwt_of([base])
+    if bwt_of([base] * 3) != "".join(c * 3 for c in one):
+        failed.append("identical_reads")
+    codes, lens = synth.uniform_reads(300, 30, 11)
+    col = oracle.Collection(codes, lens)
+    res = oracle.bwt(col, lib=lib)
+    try:
+        check_invariants(codes, lens, res["bwt"], res["dollar_pos"], res["counts"])
+    except AssertionError:
+        failed.append("invariants")
+    return failed

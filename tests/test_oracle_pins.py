@@ -1,0 +1,125 @@
+"""Pins of the CPU oracle against the paper and the mathematics (no GPU)."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import pins
+from paper_1401_7457_gb300 import synth
+
+
+def bwt_str(reads):
+    return oracle.bwt(oracle.Collection.from_strings(reads))["bwt"].decode()
+
+
+def test_figure1_worked_example():
+    """Section 2, Figure 1: {ACGT$, TAGT$, GGAA$} -> TTAAG$TAG$CAGG$, and the
+    sorted suffix columns printed under the line."""
+    reads, sorted_suffixes, want = pins.read_figure1()
+    col = oracle.Collection.from_strings(reads)
+    res = oracle.bwt(col)
+    assert res["bwt"].decode() == want
+    got_suffixes = [reads[int(i)][int(k):] + "$" for i, k in zip(res["sa_read"], res["sa_pos"])]
+    assert got_suffixes == sorted_suffixes
+
+
+@pytest.mark.parametrize("reads,want", pins.read_hand_examples())
+def test_hand_examples(reads, want):
+    assert bwt_str(reads) == want
+
+
+def test_rotation_brute_force_exhaustive_small():
+    """Every collection of one read of length <= 5, two reads of length <= 3 and
+    three reads of length <= 2 against rotation sorting."""
+    def strings(max_len):
+        for L in range(1, max_len + 1):
+            for t in itertools.product("ACGT", repeat=L):
+                yield "".join(t)
+    cases = [[s] for s in strings(5)]
+    s3 = list(strings(3))
+    cases += [[a, b] for a in s3 for b in s3]
+    s2 = list(strings(2))
+    cases += [[a, b, c] for a in s2 for b in s2 for c in s2]
+    bad = [c for c in cases if bwt_str(c) != pins.rotation_bwt(c)]
+    assert not bad, bad[:5]
+
+
+def test_rotation_brute_force_random():
+    """Random small collections, including one- and two-letter alphabets
+    (long runs of equal suffixes) and mixed read lengths."""
+    rng = np.random.default_rng(2024)
+    for _ in range(2000):
+        k = int(rng.integers(1, 7))
+        alpha = "ACGT"[: int(rng.integers(1, 5))]
+        reads = ["".join(rng.choice(list(alpha), size=int(rng.integers(1, 11)))) for _ in range(k)]
+        assert bwt_str(reads) == pins.rotation_bwt(reads), reads
+
+
+def test_single_read_is_textbook_bwt():
+    """n = 1: the BWT of S$ by sorted rotations of the single string."""
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        s = "".join(rng.choice(list("ACGT"), size=int(rng.integers(1, 40))))
+        t = s + "$"
+        rots = sorted(t[i:] + t[:i] for i in range(len(t)))  # '$' < 'A' in ASCII
+        assert bwt_str([s]) == "".join(r[-1] for r in rots)
+
+
+def test_identical_reads_closed_form():
+    """n copies of S: every symbol of BWT(S$) repeated n times."""
+    rng = np.random.default_rng(6)
+    for _ in range(50):
+        s = "".join(rng.choice(list("ACGT"), size=int(rng.integers(1, 30))))
+        n = int(rng.integers(2, 6))
+        one = bwt_str([s])
+        assert bwt_str([s] * n) == "".join(c * n for c in one)
+
+
+@pytest.mark.parametrize("case", ["uniform", "genome", "mixed", "all_a"])
+def test_invariants_moderate(case):
+    if case == "uniform":
+        codes, lens = synth.uniform_reads(2000, 100, 3)
+    elif case == "genome":
+        g = synth.random_genome(20_000, 4)
+        codes, lens = synth.sample_reads(g, 4000, 100, 5, 0.01)  # 20x coverage: long shared prefixes
+    elif case == "mixed":
+        codes, lens = synth.mixed_length_reads(3000, 1, 150, 8)
+    else:
+        codes = np.zeros(500 * 40, dtype=np.uint8)
+        lens = np.full(500, 40, dtype=np.uint32)
+    col = oracle.Collection(codes, lens)
+    res = oracle.bwt(col)
+    pins.check_invariants(codes, lens, res["bwt"], res["dollar_pos"], res["counts"])
+    assert oracle.check_sa(col, res["sa_read"], res["sa_pos"]) == -1
+
+
+def test_rank_and_certificate_agree_with_sort():
+    codes, lens = synth.mixed_length_reads(200, 1, 30, 9)
+    col = oracle.Collection(codes, lens)
+    res = oracle.bwt(col)
+    rng = np.random.default_rng(0)
+    for r in rng.integers(0, col.n_suffixes, size=50):
+        assert oracle.rank(col, int(res["sa_read"][r]), int(res["sa_pos"][r])) == r
+    sa_r, sa_p = res["sa_read"].copy(), res["sa_pos"].copy()
+    assert oracle.check_sa(col, sa_r, sa_p) == -1
+    # swapped neighbours
+    sr, sp = sa_r.copy(), sa_p.copy()
+    sr[[10, 11]] = sr[[11, 10]]
+    sp[[10, 11]] = sp[[11, 10]]
+    assert oracle.check_sa(col, sr, sp) == 10
+    # a duplicated entry
+    sr, sp = sa_r.copy(), sa_p.copy()
+    sr[20], sp[20] = sr[5], sp[5]
+    assert oracle.check_sa(col, sr, sp) >= 0
+    # wrong length
+    assert oracle.check_sa(col, sa_r[:-1], sa_p[:-1]) == -2
+
+
+def test_tiny_uniform_workload_invariants():
+    """The 10,000 x 100 bp workload end to end through the oracle (about a second)."""
+    codes, lens = synth.tiny_uniform()
+    col = oracle.Collection(codes, lens)
+    res = oracle.bwt(col)
+    assert col.n_suffixes == 1_010_000
+    pins.check_invariants(codes, lens, res["bwt"], res["dollar_pos"], res["counts"])
