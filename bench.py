@@ -1,0 +1,323 @@
+"""Benchmark: BWT build throughput (Gbase/s) of one read collection per GPU.
+
+Workload (N=1 default): 1M reads x 100 bp sampled from both strands of a
+seeded 5 Mbp random genome (20x coverage) with 1% substitutions, 101M
+suffixes.  One step = one whole ``cxbwt_build`` (histogram, every radix pass,
+emission) on device-resident input.  ``value`` = bases of all ranks / max over
+ranks of the summed device time of K steps (CUDA events on the build stream;
+L2 flushed by a 512 MB write between steps, outside the timed events).
+
+Extra keys: ``e2e`` (same metric through the C ABI with pinned host buffers,
+copies inside the timed region), ``roofline`` of the dominant kernel (the
+onesweep digit pass, 16 algorithmic bytes per suffix per pass, timed live
+with the library's own CUDA events), ``cpu_baseline`` (the oracle on a bounded
+sample on this host's cores, rank 0 only), ``clocks`` (nvidia-smi sampled
+during the timed region) and ``gpu_launches``.
+
+``--impl reference`` times the CPU oracle instead (the reference arm of this
+method is the definition itself): each step sorts a bounded sample of the same
+workload on all host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BWT build Gbases/s at 1 GB300 (% HBM roofline); served p50/p99 vs plain loop"
+UNIT = "Gbase/s"
+WORKLOAD = ("genome-like: 1,000,000 reads x 100 bp from both strands of a seeded 5 Mbp uniform genome "
+            "(20x coverage), 1% substitutions, seed 2; 101,000,000 suffixes")
+SORT_BYTES_PER_ITEM = 16  # algorithmic bytes per suffix per digit pass: 4 B key + 4 B id, read and written
+PROFILE = os.path.join(ROOT, "profiles", "onesweep_digit_pass_genome_like.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_1401_7457_gb300", "csrc", "k_sort.cu")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per item of the digit pass from the committed ncu summary,
+    or None when that summary is missing or the kernel changed since."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    m = re.search(r"dram_bytes_per_item:\s*([0-9.]+)", text)
+    s = re.search(r"k_sort_sha256:\s*([0-9a-f]+)", text)
+    if not m or not s:
+        return None
+    cur = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    if not cur.startswith(s.group(1)):
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.path:
+            return None
+        rows = []
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, flags in rows for i, f in enumerate(flags) if f.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+def cpu_oracle_rate(codes, lens, n_sample_reads, threads):
+    """Oracle throughput on the first n_sample_reads reads: (Gbase/s, seconds, bases)."""
+    import oracle
+    L = int(lens[0])
+    n_s = min(n_sample_reads, lens.size)
+    sc, sl = codes[:n_s * L], lens[:n_s]
+    col = oracle.Collection(sc, sl)
+    t0 = time.perf_counter()
+    oracle.sort(col, threads=threads)
+    dt = time.perf_counter() - t0
+    bases = int(sl.sum())
+    return bases / dt / 1e9, dt, bases
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle on a bounded sample of the workload per step."""
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1401_7457_gb300 import synth
+    oracle.build()
+    codes, lens = synth.genome_like()
+    threads = os.cpu_count() or 1
+    n_sample = args.cpu_sample_reads
+    for _ in range(args.warmup):
+        cpu_oracle_rate(codes, lens, n_sample // 4, threads)
+    times = []
+    bases = 0
+    for _ in range(args.steps):
+        _, dt, bases = cpu_oracle_rate(codes, lens, n_sample, threads)
+        times.append(dt)
+    total = sum(times)
+    value = bases * args.steps / total / 1e9
+    sample = f"first {n_sample:,} reads ({bases:,} bases) of the workload per step, std::sort / parallel-mode sort"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cxbwt", choices=["cxbwt", "reference"])
+    ap.add_argument("--cpu-sample-reads", type=int, default=300_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1401_7457_gb300 import binding, build, synth
+
+    if world > 1:
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    build.build()
+
+    # Each rank builds its own independent collection (weak scaling, no data-path collective).
+    seed = 2 if rank == 0 else synth.derive_seed(2, rank)
+    codes, lens = synth.genome_like(seed=seed)
+    words = binding.pack_codes(codes)
+    n = lens.size
+    bases = int(lens.sum())
+    N = bases + n
+    n_words = (N + 15) // 16
+
+    d_words = torch.from_numpy(words.view(np.int32)).to(dev)
+    d_lens = torch.from_numpy(lens.view(np.int32)).to(dev)
+    d_bwt = torch.empty(n_words, dtype=torch.int32, device=dev)
+    d_dpos = torch.empty(n, dtype=torch.int64, device=dev)
+    d_cnt = torch.zeros(5, dtype=torch.int64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    ctx = binding.Context(device=local, timing=True)
+
+    def step():
+        ctx.build(d_words, d_lens, d_bwt, d_dpos, d_cnt, stream=stream)
+
+    args.warmup = max(args.warmup, 3)  # at least three untimed warm-up builds
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.reset_stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)  # evict the previous step's data from L2 (outside the events)
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(ms)
+    st = ctx.stats()
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = bases * world * args.steps / (total_ms * 1e-3) / 1e9
+
+    # Dominant kernel: the onesweep digit pass.
+    pass_ms = st["sort_pass_ms"] / max(st["sort_pass_launches"], 1)
+    achieved = SORT_BYTES_PER_ITEM * N / (pass_ms * 1e-3) / 1e9
+    peak, peak_kind = peak_hbm()
+    traffic_per_item = profiled_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None if traffic_per_item is None else traffic_per_item * N,
+                "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s",
+                "kernel": "k_onesweep (LSD digit pass)", "launches_per_step": st["sort_pass_launches"] / args.steps,
+                "algorithmic_bytes_per_launch": SORT_BYTES_PER_ITEM * N, "frac_of_nominal_8tbs": achieved / 8000.0}
+    launches_per_step = st["kernel_launches"] / args.steps
+
+    # End to end through the C ABI with pinned host buffers (copies inside the timed region).
+    h_words = torch.from_numpy(words.view(np.int32)).pin_memory()
+    h_lens = torch.from_numpy(lens.view(np.int32)).pin_memory()
+    h_bwt = torch.empty(n_words, dtype=torch.int32).pin_memory()
+    h_dpos = torch.empty(n, dtype=torch.int64).pin_memory()
+    h_cnt = torch.zeros(5, dtype=torch.int64).pin_memory()
+    ctx2 = binding.Context(device=local)
+    for _ in range(2):
+        ctx2.build(h_words, h_lens, h_bwt, h_dpos, h_cnt, stream=stream)
+    ctx2.reset_stats()
+    torch.cuda.synchronize()
+    e2e_steps = max(3, min(args.steps, 10))
+    t_e2e = []
+    for _ in range(e2e_steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx2.build(h_words, h_lens, h_bwt, h_dpos, h_cnt, stream=stream)  # synchronous: returns with outputs on host
+        t_e2e.append(time.perf_counter() - t0)
+    st2 = ctx2.stats()
+    e2e_total = sum(t_e2e)
+    if world > 1:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e = {"value": bases * world * e2e_steps / e2e_total / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": st2["h2d_bytes"] // e2e_steps, "d2h_bytes_per_step": st2["d2h_bytes"] // e2e_steps,
+           "ms_per_step": e2e_total / e2e_steps * 1e3, "steps": e2e_steps}
+    ctx2.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        threads = os.cpu_count() or 1
+        rate, dt, sb = cpu_oracle_rate(codes, lens, args.cpu_sample_reads, threads)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"first {min(args.cpu_sample_reads, n):,} reads ({sb:,} bases) of the workload, "
+                         f"{dt:.1f} s wall"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n_reads": n, "read_len": int(lens[0]), "bases_per_gpu": bases,
+                           "suffixes_per_gpu": N, "l2": "flushed between steps (512 MB write outside the events)",
+                           "input": "device-resident (HBM) before the timed region; outputs left in HBM"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(st["kernel_launches"]), "gpu_launches_per_step": launches_per_step,
+                "clocks": clocks.summary(),
+                "detail": {"step_ms": ms, "sort_pass_ms_per_step": st["sort_pass_ms"] / args.steps,
+                           "build_ms_per_step_lib": st["build_ms"] / args.steps}}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

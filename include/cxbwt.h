@@ -1,0 +1,185 @@
+/*
+ * cxbwt — multi-string Burrows-Wheeler transform of short DNA reads on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The operation (Section 2 of Liu, Luo & Lam, "GPU-Accelerated BWT Construction
+ * for Large Collection of Short Reads", arXiv 1401.7457):
+ *
+ *   R = {S_0 .. S_{n-1}} is a collection of reads over A < C < G < T.  Read i
+ *   has L_i bases and is terminated by its own end marker $_i; every $ sorts
+ *   below every base and $_i < $_j whenever i < j.  All N = sum_i (L_i + 1)
+ *   suffixes (the terminator-only ones included) are sorted; B_R[r] is the
+ *   symbol that precedes the r-th smallest suffix in its read, or $ when that
+ *   suffix is the whole read.
+ *
+ * The method on the device is the paper's Section 3.2 (radix sort of suffixes
+ * by fixed-width "stringwords", moving indices instead of strings, with the
+ * variable-length / distinct-$ problem solved by padding plus a stable sort),
+ * with the stringword gathered on the GPU from a resident 2-bit read store
+ * instead of being copied from the host every iteration.
+ *
+ * Conventions used by every call below
+ * ------------------------------------
+ *  - Packed bases ("2-bit words"): base codes A=0, C=1, G=2, T=3 (the
+ *    2-bit-per-base representation of Section 3).  Base j of a packed string
+ *    occupies bits [31-2(j%16) .. 30-2(j%16)] of 32-bit word j/16 (most
+ *    significant first, so a window of bases read as an integer orders like
+ *    the string).  Reads are concatenated without padding: read i starts at
+ *    base sum_{r<i} L_r.  The buffer holds ceil(sum L / 16) words; bits past
+ *    the last base are ignored.
+ *  - Lengths: 1 <= L_i <= 65535 (the paper's reads all have m >= 1 bases).
+ *  - Pointers: every array argument may point to device memory (cudaMalloc,
+ *    cudaMallocAsync, a torch CUDA tensor) or to host memory (pageable or
+ *    pinned).  The library tells them apart with cudaPointerGetAttributes;
+ *    device inputs are used in place, never copied.
+ *  - Ownership: the caller owns every buffer passed in or out.  The library
+ *    never frees, keeps or aliases them after the call has completed.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  All device work of a call is ordered on it.  Unless the
+ *    context option `async` is set, a call returns only after its work is
+ *    complete; with it, a call returns after enqueueing when every output
+ *    is device memory; errors raised on the device by such a call are
+ *    reported by cxbwt_sync.  Calls on one context share its workspace, so
+ *    they must be issued on one stream (or synchronised in between).
+ *  - Errors: a negative cxbwt_status; cxbwt_last_error(ctx) gives a message.
+ *    Nothing throws or aborts across this boundary.  On an error the outputs
+ *    are unspecified.
+ *  - Threads: a context may be used by one host thread at a time.
+ */
+#ifndef CXBWT_H
+#define CXBWT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CXBWT_ABI_VERSION 1
+
+typedef enum {
+  CXBWT_OK = 0,
+  CXBWT_EINVAL = -1,        /* bad argument: NULL pointer, n_reads == 0, a length of 0 or > 65535 */
+  CXBWT_ENOMEM = -2,        /* device memory or the context's device budget is exhausted */
+  CXBWT_ECUDA = -3,         /* a CUDA runtime call failed */
+  CXBWT_ETIMEOUT = -4,      /* a device-side wait gave up after its time limit (no hang, no trap) */
+  CXBWT_EUNSUPPORTED = -5,  /* a size the current build does not handle */
+  CXBWT_EBUSY = -6,         /* serving: no slot or budget free (only from non-blocking calls) */
+  CXBWT_EINTERNAL = -7      /* an internal consistency check failed */
+} cxbwt_status;
+
+typedef struct cxbwt_ctx cxbwt_ctx;
+
+/* Options of a context.  Zero in any field selects the default. */
+typedef struct {
+  uint64_t device_budget_bytes; /* cap on device memory the context may hold; 0 = 90% of free memory */
+  int device;                   /* CUDA device ordinal */
+  int prefix_len;               /* l of the bucket plan (Section 3.1); 0 = automatic */
+  int digit_bits;               /* radix digit width; 8 is the only width built (0 = 8) */
+  int tile_items;               /* items per radix tile; 0 = automatic */
+  int async;                    /* nonzero: calls return after enqueue when outputs are on the device */
+  int timing;                   /* nonzero: record CUDA events around every phase (see cxbwt_stats) */
+  int reserved[8];
+} cxbwt_options;
+
+/* Counters accumulated by a context since creation or cxbwt_reset_stats. */
+typedef struct {
+  uint64_t builds;              /* completed builds */
+  uint64_t bases;               /* sum of read lengths over those builds */
+  uint64_t suffixes;            /* sum of N over those builds */
+  uint64_t kernel_launches;     /* kernels this library launched */
+  uint64_t sort_pass_launches;  /* radix digit passes among them */
+  uint64_t sort_pass_items;     /* sum over digit passes of the items each one moved */
+  double sort_pass_ms;          /* device time of the digit passes (only with `timing`) */
+  double build_ms;              /* device time of whole builds (only with `timing`) */
+  uint64_t h2d_bytes;           /* bytes this library copied host -> device */
+  uint64_t d2h_bytes;           /* bytes this library copied device -> host */
+  uint64_t device_bytes_held;   /* device memory the context holds now */
+  uint64_t reserved[7];
+} cxbwt_stats;
+
+/* ABI version of the loaded library (CXBWT_ABI_VERSION it was built with). */
+int cxbwt_abi_version(void);
+
+/* Fills *opt with the defaults. */
+void cxbwt_default_options(cxbwt_options* opt);
+
+/* Creates a context on opt->device (NULL opt = defaults).  The context owns
+ * the device workspace (grown on demand within the budget and reused across
+ * calls) and the per-call bookkeeping.  *out is set to NULL on failure. */
+int cxbwt_create(cxbwt_ctx** out, const cxbwt_options* opt);
+
+/* Waits for the context's outstanding work, frees everything it holds. NULL is a no-op. */
+void cxbwt_destroy(cxbwt_ctx* ctx);
+
+/* Message of the last error on ctx ("" if none); with ctx == NULL, the last
+ * error of a failed cxbwt_create on this thread.  Valid until the next call. */
+const char* cxbwt_last_error(const cxbwt_ctx* ctx);
+
+/* Name of a status code. */
+const char* cxbwt_status_string(int status);
+
+/* Sizes of the outputs of a build of n_reads reads with host lengths `lens`:
+ * *n_symbols = N = n_reads + sum(lens); *bwt_words = ceil(N / 16).
+ * Either output pointer may be NULL. */
+int cxbwt_output_size(uint64_t n_reads, const uint32_t* lens_host, uint64_t* n_symbols, uint64_t* bwt_words);
+
+/* Builds the BWT of one read collection (Section 2 definition; Section 3.2 method).
+ *
+ *   reads_2bit      packed bases of all reads (layout above), ceil(sum L / 16) words
+ *   n_reads         n >= 1
+ *   lens            n read lengths (uint32)
+ *   out_bwt         ceil(N / 16) words: B_R packed 2 bits per symbol in the
+ *                   same layout; a $ symbol is stored as code 0 (its position
+ *                   is given by out_dollar_pos).  Padding bits are 0.
+ *   out_dollar_pos  n entries (may be NULL): out_dollar_pos[i] is the row r of
+ *                   B_R holding the $ that precedes read i as a whole suffix,
+ *                   i.e. the rank of suffix (i, 0).  These n rows are exactly
+ *                   the $ symbols of B_R.
+ *   out_counts      5 entries (may be NULL): occurrences of $, A, C, G, T in
+ *                   B_R.  The FM-index array C[c] is their exclusive prefix sum.
+ *
+ * Returns CXBWT_OK, or CXBWT_EINVAL / ENOMEM / ECUDA / ETIMEOUT / EUNSUPPORTED. */
+int cxbwt_build(cxbwt_ctx* ctx, const uint32_t* reads_2bit, uint64_t n_reads, const uint32_t* lens,
+                uint32_t* out_bwt, uint64_t* out_dollar_pos, uint64_t* out_counts, void* stream);
+
+/* cxbwt_build that also returns the sorted suffix list:
+ *   out_sa          N entries: out_sa[r] = (i << 16) | k for the suffix
+ *                   S_i[k..] $_i of rank r (k = L_i is the terminator-only one).
+ * Meant for verification (a sortedness certificate at any size) and for
+ * callers that sample the suffix array; it costs 8 extra bytes per suffix. */
+int cxbwt_build_sa(cxbwt_ctx* ctx, const uint32_t* reads_2bit, uint64_t n_reads, const uint32_t* lens,
+                   uint32_t* out_bwt, uint64_t* out_dollar_pos, uint64_t* out_counts, uint64_t* out_sa,
+                   void* stream);
+
+/* Waits for the context's outstanding work and returns the first error a
+ * device-side check recorded since the last call (CXBWT_OK if none). */
+int cxbwt_sync(cxbwt_ctx* ctx);
+
+/* Statistics (see cxbwt_stats). */
+int cxbwt_get_stats(const cxbwt_ctx* ctx, cxbwt_stats* out);
+int cxbwt_reset_stats(cxbwt_ctx* ctx);
+
+/* ---- host helpers (no device work) ---------------------------------------- */
+
+/* Packs n_bases base codes (uint8 0..3) into ceil(n_bases/16) words, layout
+ * above.  EINVAL on a code > 3. */
+int cxbwt_pack_codes(const uint8_t* codes, uint64_t n_bases, uint32_t* out_words);
+
+/* Same from ASCII "ACGT" (upper case).  EINVAL on any other character
+ * (reads must be pre-filtered: the paper's reads contain only A, C, G, T). */
+int cxbwt_pack_ascii(const char* acgt, uint64_t n_bases, uint32_t* out_words);
+
+/* Expands a packed BWT of n_symbols symbols to ASCII over "$ACGT": symbol r is
+ * '$' if r is one of the n_dollars entries of dollar_pos (any order), else
+ * the base its code names.  out holds n_symbols bytes (no terminator).
+ * EINVAL on a dollar position >= n_symbols. */
+int cxbwt_unpack_ascii(const uint32_t* bwt_words, const uint64_t* dollar_pos, uint64_t n_symbols,
+                       uint64_t n_dollars, char* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CXBWT_H */

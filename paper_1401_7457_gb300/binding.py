@@ -1,0 +1,275 @@
+"""ctypes binding of libcxbwt (include/cxbwt.h): argument marshalling only.
+
+Every step of a build runs in the CUDA library; this module only turns numpy
+arrays and torch tensors into pointers, allocates outputs when the caller
+does not pass them, and raises ``CxbwtError`` on a negative status.  If the
+library has not been built, importing the functions below raises: there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libcxbwt.so")
+
+_lock = threading.Lock()
+_lib = None
+
+STATUS = {0: "CXBWT_OK", -1: "CXBWT_EINVAL", -2: "CXBWT_ENOMEM", -3: "CXBWT_ECUDA", -4: "CXBWT_ETIMEOUT",
+          -5: "CXBWT_EUNSUPPORTED", -6: "CXBWT_EBUSY", -7: "CXBWT_EINTERNAL"}
+
+
+class CxbwtError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("device_budget_bytes", ctypes.c_uint64), ("device", ctypes.c_int), ("prefix_len", ctypes.c_int),
+                ("digit_bits", ctypes.c_int), ("tile_items", ctypes.c_int), ("async_", ctypes.c_int),
+                ("timing", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("builds", ctypes.c_uint64), ("bases", ctypes.c_uint64), ("suffixes", ctypes.c_uint64),
+                ("kernel_launches", ctypes.c_uint64), ("sort_pass_launches", ctypes.c_uint64),
+                ("sort_pass_items", ctypes.c_uint64), ("sort_pass_ms", ctypes.c_double),
+                ("build_ms", ctypes.c_double), ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
+                ("device_bytes_held", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 7)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+# Every entry point of include/cxbwt.h with its ctypes signature.
+_VP, _U64, _U32P, _U64P = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p
+SIGNATURES = {
+    "cxbwt_abi_version": (ctypes.c_int, []),
+    "cxbwt_default_options": (None, [ctypes.POINTER(Options)]),
+    "cxbwt_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(Options)]),
+    "cxbwt_destroy": (None, [_VP]),
+    "cxbwt_last_error": (ctypes.c_char_p, [_VP]),
+    "cxbwt_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "cxbwt_output_size": (ctypes.c_int, [_U64, _VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+    "cxbwt_build": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP, _VP, _VP, _VP]),
+    "cxbwt_build_sa": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "cxbwt_sync": (ctypes.c_int, [_VP]),
+    "cxbwt_get_stats": (ctypes.c_int, [_VP, ctypes.POINTER(Stats)]),
+    "cxbwt_reset_stats": (ctypes.c_int, [_VP]),
+    "cxbwt_pack_codes": (ctypes.c_int, [_VP, _U64, _VP]),
+    "cxbwt_pack_ascii": (ctypes.c_int, [ctypes.c_char_p, _U64, _VP]),
+    "cxbwt_unpack_ascii": (ctypes.c_int, [_VP, _VP, _U64, _U64, _VP]),
+}
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libcxbwt is not built ({LIB_PATH} missing): run __graft_entry__.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_tensor(x):
+    try:
+        import torch
+    except ImportError:
+        return False
+    return isinstance(x, torch.Tensor)
+
+
+def _ptr(x):
+    """Pointer of a numpy array or torch tensor (must be contiguous)."""
+    if x is None:
+        return None
+    if _is_tensor(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"expected numpy array or torch tensor, got {type(x)}")
+
+
+def _nbytes(x):
+    return x.numel() * x.element_size() if _is_tensor(x) else x.nbytes
+
+
+def _check(status: int, ctx=None):
+    if status != 0:
+        msg = lib().cxbwt_last_error(ctx)
+        raise CxbwtError(status, msg.decode() if msg else "")
+
+
+# ---- host helpers -----------------------------------------------------------
+
+def pack_codes(codes: np.ndarray) -> np.ndarray:
+    """Base codes (uint8, 0..3) -> packed 2-bit words (uint32, ABI layout)."""
+    codes = np.ascontiguousarray(codes, dtype=np.uint8)
+    out = np.zeros((codes.size + 15) // 16, dtype=np.uint32)
+    _check(lib().cxbwt_pack_codes(codes.ctypes.data, codes.size, out.ctypes.data))
+    return out
+
+
+def pack_ascii(s: str | bytes) -> np.ndarray:
+    b = s.encode() if isinstance(s, str) else bytes(s)
+    out = np.zeros((len(b) + 15) // 16, dtype=np.uint32)
+    _check(lib().cxbwt_pack_ascii(b, len(b), out.ctypes.data))
+    return out
+
+
+def unpack_ascii(words, dollar_pos, n_symbols: int) -> bytes:
+    """Packed BWT + $ rows -> ASCII bytes over $ACGT."""
+    words = np.ascontiguousarray(_to_numpy(words).view(np.uint32))
+    dp = np.ascontiguousarray(_to_numpy(dollar_pos).view(np.uint64))
+    out = ctypes.create_string_buffer(max(int(n_symbols), 1))
+    _check(lib().cxbwt_unpack_ascii(words.ctypes.data, dp.ctypes.data, int(n_symbols), dp.size, out))
+    return out.raw[:int(n_symbols)]
+
+
+def output_size(lens) -> tuple[int, int]:
+    lens = np.ascontiguousarray(_to_numpy(lens).view(np.uint32))
+    n_sym, words = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().cxbwt_output_size(lens.size, lens.ctypes.data, ctypes.byref(n_sym), ctypes.byref(words)))
+    return int(n_sym.value), int(words.value)
+
+
+def _to_numpy(x):
+    if _is_tensor(x):
+        return x.detach().cpu().numpy()
+    return np.asarray(x)
+
+
+# ---- context ----------------------------------------------------------------
+
+class Context:
+    """One cxbwt context (device workspace + bookkeeping) on one device."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0, async_: bool = False, timing: bool = False,
+                 tile_items: int = 0):
+        L = lib()
+        opt = Options()
+        L.cxbwt_default_options(ctypes.byref(opt))
+        opt.device = device
+        opt.device_budget_bytes = budget_bytes
+        opt.async_ = 1 if async_ else 0
+        opt.timing = 1 if timing else 0
+        opt.tile_items = tile_items
+        h = ctypes.c_void_p()
+        st = L.cxbwt_create(ctypes.byref(h), ctypes.byref(opt))
+        if st != 0:
+            raise CxbwtError(st, (L.cxbwt_last_error(None) or b"").decode())
+        self._h = h
+        self.device = device
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cxbwt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def build(self, reads_2bit, lens, out_bwt=None, out_dollar_pos=None, out_counts=None, out_sa=None,
+              stream=None, want_sa: bool = False):
+        """Build the BWT.  Inputs may be numpy arrays (host) or torch tensors
+        (host or CUDA); missing outputs are allocated on the inputs' side.
+        Returns ``(bwt_words, dollar_pos, counts[, sa])``."""
+        n = int(lens.numel() if _is_tensor(lens) else np.asarray(lens).size)
+        on_dev = _is_tensor(reads_2bit) and reads_2bit.is_cuda
+        if out_bwt is None or out_dollar_pos is None or out_counts is None or (want_sa and out_sa is None):
+            if _is_tensor(lens) and lens.is_cuda:
+                total = int(lens.to(dtype=_torch().int64).sum().item()) + n
+            else:
+                total = int(np.asarray(_to_numpy(lens), dtype=np.uint64).sum()) + n
+            words = (total + 15) // 16
+            if on_dev:
+                torch = _torch()
+                dev = reads_2bit.device
+                if out_bwt is None:
+                    out_bwt = torch.empty(words, dtype=torch.int32, device=dev)
+                if out_dollar_pos is None:
+                    out_dollar_pos = torch.empty(n, dtype=torch.int64, device=dev)
+                if out_counts is None:
+                    out_counts = torch.zeros(5, dtype=torch.int64, device=dev)
+                if want_sa and out_sa is None:
+                    out_sa = torch.empty(total, dtype=torch.int64, device=dev)
+            else:
+                if out_bwt is None:
+                    out_bwt = np.zeros(words, dtype=np.uint32)
+                if out_dollar_pos is None:
+                    out_dollar_pos = np.zeros(n, dtype=np.uint64)
+                if out_counts is None:
+                    out_counts = np.zeros(5, dtype=np.uint64)
+                if want_sa and out_sa is None:
+                    out_sa = np.zeros(total, dtype=np.uint64)
+        st = _stream_ptr(stream)
+        L = lib()
+        if want_sa or out_sa is not None:
+            status = L.cxbwt_build_sa(self._h, _ptr(reads_2bit), n, _ptr(lens), _ptr(out_bwt), _ptr(out_dollar_pos),
+                                      _ptr(out_counts), _ptr(out_sa), st)
+            _check(status, self._h)
+            return out_bwt, out_dollar_pos, out_counts, out_sa
+        status = L.cxbwt_build(self._h, _ptr(reads_2bit), n, _ptr(lens), _ptr(out_bwt), _ptr(out_dollar_pos),
+                               _ptr(out_counts), st)
+        _check(status, self._h)
+        return out_bwt, out_dollar_pos, out_counts
+
+    def sync(self):
+        _check(lib().cxbwt_sync(self._h), self._h)
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().cxbwt_get_stats(self._h, ctypes.byref(s)), self._h)
+        return s.as_dict()
+
+    def reset_stats(self):
+        _check(lib().cxbwt_reset_stats(self._h), self._h)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+def decode_sa(sa) -> tuple[np.ndarray, np.ndarray]:
+    """(i << 16) | k entries -> (read, offset) arrays."""
+    a = _to_numpy(sa).view(np.uint64)
+    return a >> np.uint64(16), (a & np.uint64(0xFFFF)).astype(np.uint32)

@@ -1,0 +1,170 @@
+// Whole-collection counts computed before the digit passes.
+//
+// Step 1 of the paper's Figure 2 scans every suffix once to size its
+// partitions; here one scan of the read store yields, for every digit
+// position d of the LSD sort, how many suffixes carry each digit value.  That
+// is the all-digit histogram of onesweep: each pass then knows the first
+// output row of every digit value before it starts.
+//
+// Counting suffixes directly would cost N * D digit extractions.  Instead:
+// the digit d of suffix (i, k) is the 4-mer of read i at position q = k + 4d
+// (A-padded), so with P[q][v] = #{reads i : q < L_i, 4-mer_i(q) = v},
+//   hist_d[v] = sum_{q >= 4d} P[q][v] + [v = 0] * Z_d,
+//   Z_d       = sum_i (L_i + 1 - max(0, L_i - 4d))   (suffixes whose digit d
+//               lies wholly past the end of the read),
+// which needs one pass over the bases (sum L_i counter increments).
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace cxbwt {
+namespace {
+
+constexpr int kSlab = 64;            // read positions per CTA slab: 64 x 256 counters = 64 KB
+constexpr int kCountThreads = 512;
+
+__global__ void __launch_bounds__(kCountThreads) k_poscount(const ReadIndex R, uint32_t n_reads, uint32_t q_max,
+                                                            uint32_t* __restrict__ P) {
+  extern __shared__ uint32_t sP[];
+  const uint32_t q0 = blockIdx.y * kSlab;
+  const uint32_t qn = min(uint32_t(kSlab), q_max - q0);
+  for (uint32_t x = threadIdx.x; x < qn * kRadix; x += blockDim.x) sP[x] = 0u;
+  __syncthreads();
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n_reads; r += gridDim.x * blockDim.x) {
+    Suffix s = decode(R, r << R.shift);  // whole read (k = 0)
+    const uint32_t qe = min(q0 + qn, s.len);
+    for (uint32_t q = q0; q < qe; q += 16) {
+      // Bases q .. q+31 (A-padded): every 4-mer starting in q .. q+15.
+      const uint64_t win = (uint64_t(window16(R, s, q)) << 32) | window16(R, s, q + 16);
+      const uint32_t tn = min(16u, qe - q);
+      for (uint32_t t = 0; t < tn; ++t) {
+        const uint32_t mer = uint32_t(win >> (56 - 2 * t)) & (kRadix - 1);
+        atomicAdd(&sP[(q + t - q0) * kRadix + mer], 1u);
+      }
+    }
+  }
+  __syncthreads();
+  for (uint32_t x = threadIdx.x; x < qn * kRadix; x += blockDim.x) {
+    const uint32_t v = sP[x];
+    if (v) atomicAdd(&P[uint64_t(q0) * kRadix + x], v);
+  }
+}
+
+__device__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* scratch /*[blockDim/32]*/) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t incl = x;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) scratch[warp] = incl;
+  __syncthreads();
+  uint32_t pre = 0;
+  for (int w = 0; w < nw; ++w)
+    if (w < warp) pre += scratch[w];
+  return pre + incl - x;
+}
+
+__global__ void __launch_bounds__(kRadix) k_digitbase(const uint32_t* __restrict__ P, uint32_t q_max, int uniform,
+                                                      uint32_t n_reads, uint32_t uniform_len,
+                                                      const uint32_t* __restrict__ lenhist, uint32_t* __restrict__ base) {
+  __shared__ unsigned long long s_z[kRadix / 32];
+  __shared__ uint32_t s_scan[kRadix / 32];
+  const uint32_t d = blockIdx.x, v = threadIdx.x;
+  const uint32_t lo = 4u * d;
+  uint32_t h = 0;
+  for (uint32_t q = lo; q < q_max; ++q) h += P[uint64_t(q) * kRadix + v];
+  // Z_d: suffixes whose digit d is entirely padding.
+  unsigned long long z = 0;
+  if (uniform) {
+    z = (unsigned long long)n_reads * (uniform_len + 1u - (uniform_len > lo ? uniform_len - lo : 0u));
+  } else {
+    for (uint32_t l = v; l <= q_max; l += blockDim.x)
+      z += (unsigned long long)lenhist[l] * (l + 1u - (l > lo ? l - lo : 0u));
+    for (int o = 16; o > 0; o >>= 1) z += __shfl_down_sync(0xFFFFFFFFu, z, o);
+    if ((v & 31) == 0) s_z[v >> 5] = z;
+    __syncthreads();
+    z = 0;
+    for (int w = 0; w < kRadix / 32; ++w) z += s_z[w];
+  }
+  if (v == 0) h += uint32_t(z);
+  base[uint64_t(d) * kRadix + v] = block_exclusive_scan(h, s_scan);
+}
+
+__global__ void k_identity(const ReadIndex R, uint32_t n_reads, uint32_t* __restrict__ vals) {
+  // One warp per read: vals[off_i + i + k] = (i << shift) | k, k = 0 .. L_i.
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31;
+  for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n_reads; i += warps) {
+    const Suffix s = decode(R, i << R.shift);
+    const uint64_t row0 = s.off + i;
+    for (uint32_t k = lane; k <= s.len; k += 32) vals[row0 + k] = (i << R.shift) | k;
+  }
+}
+
+__global__ void k_lenstats(const uint32_t* __restrict__ lens, uint64_t n, unsigned long long* out) {
+  unsigned long long mn = ~0ull, mx = 0, sum = 0, bad = 0;
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += uint64_t(gridDim.x) * blockDim.x) {
+    const uint32_t L = lens[i];
+    mn = min(mn, (unsigned long long)L);
+    mx = max(mx, (unsigned long long)L);
+    sum += L;
+    bad += (L == 0u || L > 65535u) ? 1u : 0u;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = min(mn, __shfl_down_sync(0xFFFFFFFFu, mn, o));
+    mx = max(mx, __shfl_down_sync(0xFFFFFFFFu, mx, o));
+    sum += __shfl_down_sync(0xFFFFFFFFu, sum, o);
+    bad += __shfl_down_sync(0xFFFFFFFFu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(out + 0, mn);
+    atomicMax(out + 1, mx);
+    atomicAdd(out + 2, sum);
+    atomicAdd(out + 3, bad);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_poscount(const ReadIndex& R, uint32_t n_reads, uint32_t q_max, uint32_t* P, int sm_count,
+                            cudaStream_t st) {
+  if (q_max == 0 || n_reads == 0) return cudaSuccess;
+  const size_t smem = size_t(kSlab) * kRadix * sizeof(uint32_t);
+  cudaError_t e = cudaFuncSetAttribute(k_poscount, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  const uint32_t slabs = (q_max + kSlab - 1) / kSlab;
+  uint32_t gx = (n_reads + kCountThreads - 1) / kCountThreads;
+  const uint32_t cap = max(1u, uint32_t(2 * sm_count) / slabs);
+  if (gx > cap) gx = cap;
+  k_poscount<<<dim3(gx, slabs), kCountThreads, smem, st>>>(R, n_reads, q_max, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_digitbase(const uint32_t* P, uint32_t q_max, uint32_t D, int uniform, uint32_t n_reads,
+                             uint32_t uniform_len, const uint32_t* lenhist, uint32_t* base, cudaStream_t st) {
+  if (D == 0) return cudaSuccess;
+  k_digitbase<<<D, kRadix, 0, st>>>(P, q_max, uniform, n_reads, uniform_len, lenhist, base);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_identity(const ReadIndex& R, uint32_t n_reads, const uint64_t* /*unused*/, uint32_t* vals,
+                            cudaStream_t st) {
+  if (n_reads == 0) return cudaSuccess;
+  const uint32_t threads = 256;
+  uint64_t blocks = (uint64_t(n_reads) * 32 + threads - 1) / threads;
+  if (blocks > 65535u * 4u) blocks = 65535u * 4u;
+  k_identity<<<uint32_t(blocks), threads, 0, st>>>(R, n_reads, vals);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lenstats(const uint32_t* lens, uint64_t n, unsigned long long* out, cudaStream_t st) {
+  const uint32_t threads = 256;
+  uint64_t blocks = (n + threads - 1) / threads;
+  if (blocks > 1024) blocks = 1024;
+  if (blocks == 0) blocks = 1;
+  k_lenstats<<<uint32_t(blocks), threads, 0, st>>>(lens, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace cxbwt

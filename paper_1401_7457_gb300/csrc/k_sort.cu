@@ -1,0 +1,262 @@
+// One stable LSD digit pass over (key, value) items: the "onesweep" scheme
+// (Adinets & Merrill 2022) written for sm_103a.
+//
+// This is the radix sort at the core of Section 3.2 of the paper ("sort by
+// index": the values are 32-bit suffix ids; the keys are 16-base stringwords,
+// 8 bits = 4 bases per pass, least significant first).  The paper called a
+// library sort and permuted each new stringword by index on the host side of
+// PCIe; here the stringword is gathered from the device-resident read store
+// inside the first pass of each 16-base window (kSrcExtract), and carried in
+// the key array for the other passes of that window.
+//
+// One CTA sorts one tile of threads*IPT items:
+//   1. take a tile id from an atomic counter (so every lower tile is already
+//      running: the look-back below always makes progress),
+//   2. load the tile (warp-striped, coalesced) and compute each item's digit,
+//   3. rank items inside the tile: warp-level __match_any_sync groups equal
+//      digits; a per-warp shared-memory histogram accumulates counts in item
+//      order, so the ranking is stable,
+//   4. publish the tile's per-digit counts, then walk back over the
+//      predecessors' published counts (decoupled look-back) to find, for each
+//      digit, how many items of earlier tiles precede this tile; the first row
+//      of each digit comes from the all-tile histogram computed before the
+//      pass (digit_base),
+//   5. stage the tile in shared memory in sorted order and write it out, so
+//      that runs of equal digits go to consecutive addresses.
+// The only wait is in step 4.  It is bounded by a wall-clock limit; when the
+// limit passes the kernel records kErrTimeout and finishes (it never traps).
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace cxbwt {
+namespace {
+
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t x, uint32_t* scratch /*[8]*/) {
+  // Threads 0..255 hold one value each; returns their exclusive prefix sum.
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (tid < 256 && lane == 31) scratch[warp] = incl;
+  __syncthreads();
+  uint32_t warp_prefix = 0;
+  if (tid < 256) {
+#pragma unroll
+    for (int w = 0; w < 8; ++w)
+      if (w < warp) warp_prefix += scratch[w];
+  }
+  return warp_prefix + incl - x;
+}
+
+template <int THREADS, int IPT, int MODE, bool WRITE_KEY>
+__global__ void __launch_bounds__(THREADS) k_onesweep(const PassArgs a) {
+  constexpr int TILE = THREADS * IPT;
+  constexpr int WARPS = THREADS / 32;
+  static_assert(THREADS >= 256 && THREADS % 32 == 0, "one thread per digit value is needed");
+
+  extern __shared__ __align__(16) uint32_t s_stage[];  // keys [TILE], then values [TILE]
+  uint32_t* s_keys = s_stage;
+  uint32_t* s_vals = s_stage + TILE;
+  __shared__ uint32_t s_whist[WARPS][kRadix];  // per-warp digit counts, then per-warp offsets
+  __shared__ uint32_t s_dexcl[kRadix];         // tile-local first row of each digit
+  __shared__ uint32_t s_gbase[kRadix];         // global row of tile-local row 0 of each digit
+  __shared__ uint32_t s_scan[8];
+  __shared__ uint32_t s_tile;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < WARPS * kRadix; i += THREADS) (&s_whist[0][0])[i] = 0u;
+  if (tid == 0) {
+    const uint32_t t = atomicAdd(a.tile_counter, 1u);
+    // Every id has been handed out once the last one is: reset for the next pass.
+    if (t == a.n_tiles - 1) atomicExch(a.tile_counter, 0u);
+    s_tile = t;
+  }
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint64_t tile_base = uint64_t(tile) * TILE;
+  const uint64_t warp_base = tile_base + uint64_t(warp) * 32 * IPT;
+
+  uint32_t key[IPT], val[IPT], digit[IPT], rank[IPT];
+
+  // ---- 2. load ------------------------------------------------------------
+  if (MODE == kSrcInitUniform) {
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const uint64_t idx = warp_base + j * 32 + lane;
+      const uint32_t L = a.R.uniform_len;
+      // Position idx of the (suffix length, read) order: length idx / n, read idx % n.
+      const uint32_t slen = uint32_t(idx / a.n_reads);
+      const uint32_t i = uint32_t(idx - uint64_t(slen) * a.n_reads);
+      val[j] = (i << a.R.shift) | (L - min(slen, L));
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const uint64_t idx = warp_base + j * 32 + lane;
+      val[j] = idx < a.n_items ? __ldg(a.vals_in + idx) : 0u;
+    }
+  }
+  if (MODE == kSrcCarried) {
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const uint64_t idx = warp_base + j * 32 + lane;
+      key[j] = idx < a.n_items ? __ldg(a.keys_in + idx) : 0u;
+    }
+  } else if (MODE == kSrcLength) {
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const Suffix s = decode(a.R, val[j]);
+      key[j] = s.len - s.k;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const uint64_t idx = warp_base + j * 32 + lane;
+      key[j] = idx < a.n_items ? window16(a.R, decode(a.R, val[j]), a.window_c0) : 0u;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < IPT; ++j) {
+    const uint64_t idx = warp_base + j * 32 + lane;
+    // Items past the end get a value no digit has, so they match only each other.
+    digit[j] = idx < a.n_items ? ((key[j] >> a.key_shift) & (kRadix - 1)) : uint32_t(kRadix);
+  }
+
+  // ---- 3. stable rank inside the warp, in item order ------------------------
+  const uint32_t lt = lanemask_lt();
+#pragma unroll
+  for (int j = 0; j < IPT; ++j) {
+    const uint32_t d = digit[j];
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+    const int leader = __ffs(peers) - 1;
+    uint32_t prior = 0;
+    if (lane == leader && d < kRadix) {
+      prior = s_whist[warp][d];
+      s_whist[warp][d] = prior + __popc(peers);
+    }
+    prior = __shfl_sync(0xFFFFFFFFu, prior, leader);
+    rank[j] = prior + __popc(peers & lt);
+    __syncwarp();
+  }
+  __syncthreads();
+
+  // ---- 4. tile counts, look-back --------------------------------------------
+  uint32_t tile_cnt = 0;
+  if (tid < kRadix) {
+    uint32_t sum = 0;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) {
+      const uint32_t c = s_whist[w][tid];
+      s_whist[w][tid] = sum;
+      sum += c;
+    }
+    tile_cnt = sum;
+    const unsigned long long agg_flag = (unsigned long long)(2u * a.epoch) << 32;
+    const unsigned long long pre_flag = (unsigned long long)(2u * a.epoch + 1u) << 32;
+    store_relaxed_u64(a.status + uint64_t(tile) * kRadix + tid, (tile == 0 ? pre_flag : agg_flag) | tile_cnt);
+  }
+  const uint32_t local_excl = block_exclusive_scan_256<THREADS>(tile_cnt, s_scan);
+  if (tid < kRadix) {
+    s_dexcl[tid] = local_excl;
+    uint32_t before = 0;  // items with this digit in tiles 0 .. tile-1
+    if (tile > 0) {
+      const uint32_t agg = 2u * a.epoch, pre = 2u * a.epoch + 1u;
+      int64_t p = int64_t(tile) - 1;
+      uint64_t t0 = 0;
+      uint32_t spins = 0;
+      while (p >= 0) {
+        const unsigned long long s = load_relaxed_u64(a.status + uint64_t(p) * kRadix + tid);
+        const uint32_t flag = uint32_t(s >> 32);
+        if (flag != agg && flag != pre) {  // not yet published in this pass
+          if ((++spins & 63u) == 0u) {
+            const uint64_t now = global_timer_ns();
+            if (t0 == 0) {
+              t0 = now;
+            } else if (now - t0 > a.timeout_ns) {
+              atomicOr(a.err, kErrTimeout);
+              break;
+            }
+          }
+          continue;
+        }
+        before += uint32_t(s);
+        if (flag == pre) break;
+        --p;
+      }
+      store_relaxed_u64(a.status + uint64_t(tile) * kRadix + tid,
+                        ((unsigned long long)(2u * a.epoch + 1u) << 32) | (before + tile_cnt));
+    }
+    s_gbase[tid] = __ldg(a.digit_base + tid) + before - local_excl;
+  }
+  __syncthreads();
+
+  // ---- 5. stage sorted in shared memory, write out --------------------------
+#pragma unroll
+  for (int j = 0; j < IPT; ++j) {
+    const uint32_t d = digit[j];
+    if (d < kRadix) {
+      const uint32_t r = s_dexcl[d] + s_whist[warp][d] + rank[j];
+      s_keys[r] = key[j];
+      s_vals[r] = val[j];
+    }
+  }
+  __syncthreads();
+  const uint64_t left = uint64_t(a.n_items) - tile_base;
+  const uint32_t n_valid = left < uint64_t(TILE) ? uint32_t(left) : uint32_t(TILE);
+#pragma unroll
+  for (int j = 0; j < IPT; ++j) {
+    const uint32_t r = j * THREADS + tid;
+    if (r < n_valid) {
+      const uint32_t k = s_keys[r];
+      const uint32_t d = (k >> a.key_shift) & (kRadix - 1);
+      const uint32_t g = s_gbase[d] + r;
+      if (g < a.n_items) {
+        a.vals_out[g] = s_vals[r];
+        if (WRITE_KEY) a.keys_out[g] = k;
+      } else {
+        atomicOr(a.err, kErrBounds);  // digit bases disagree with the items: never write out of bounds
+      }
+    }
+  }
+}
+
+constexpr int kThreads = 256;
+constexpr int kIpt = 16;
+
+template <int MODE, bool WK>
+cudaError_t launch_mode(const PassArgs& a, const TileShape& s, cudaStream_t st) {
+  const size_t smem = onesweep_smem_bytes(s);
+  auto kern = k_onesweep<kThreads, kIpt, MODE, WK>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  kern<<<a.n_tiles, kThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+TileShape onesweep_shape(int /*tile_items_hint*/) { return TileShape{kThreads, kIpt}; }
+
+size_t onesweep_smem_bytes(const TileShape& s) { return size_t(s.tile()) * 2 * sizeof(uint32_t); }
+
+cudaError_t launch_onesweep(const PassArgs& a, int mode, bool write_key, const TileShape& s, cudaStream_t st) {
+  if (a.n_tiles == 0) return cudaSuccess;
+  switch (mode) {
+    case kSrcInitUniform: return write_key ? launch_mode<kSrcInitUniform, true>(a, s, st)
+                                           : launch_mode<kSrcInitUniform, false>(a, s, st);
+    case kSrcExtract: return write_key ? launch_mode<kSrcExtract, true>(a, s, st)
+                                       : launch_mode<kSrcExtract, false>(a, s, st);
+    case kSrcCarried: return write_key ? launch_mode<kSrcCarried, true>(a, s, st)
+                                       : launch_mode<kSrcCarried, false>(a, s, st);
+    case kSrcLength: return write_key ? launch_mode<kSrcLength, true>(a, s, st)
+                                      : launch_mode<kSrcLength, false>(a, s, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace cxbwt

@@ -65,12 +65,25 @@ def read_hand_examples():
     return out
 
 
-def lf_invert(bwt: bytes, n: int, max_len: int):
-    """Recover every read from the BWT by LF-mapping.
+def lf_walk(bwt: bytes, n: int, max_len: int):
+    """LF walks from rows 0..n-1: an (n, max_len) matrix of the base codes met
+    (read i last base first), -1 after the walk met $, and the $ rows."""
+    rev, end_rows, M = _lf(bwt, n, max_len)
+    return M, end_rows
 
-    Returns ``(reads_reversed, end_rows)``: for each read i, its bases in
-    reverse order as a list of uint8 arrays of codes, and the row at which the
-    walk met $.  Raises if a walk does not meet $ within ``max_len + 1`` steps.
+
+def lf_invert(bwt: bytes, n: int, max_len: int):
+    rev, end_rows, _ = _lf(bwt, n, max_len)
+    return rev, end_rows
+
+
+def _lf(bwt: bytes, n: int, max_len: int):
+    """Recover every read from the BWT by LF-mapping, LF(r) = C[c] + rank_c(r).
+
+    Returns ``(reads_reversed, end_rows, M)``: for each read i (when n is
+    small) its bases in reverse order, the row at which the walk met $, and the
+    int8 walk matrix.  Raises if a walk does not meet $ within ``max_len + 1``
+    steps.
     """
     B = np.frombuffer(bwt, dtype=np.uint8)
     lut = np.full(256, 255, dtype=np.uint8)
@@ -98,17 +111,17 @@ def lf_invert(bwt: bytes, n: int, max_len: int):
         active &= s != 0
         if not active.any():
             break
-        step = np.where(active, s.astype(np.int64) - 1, -1)
+        step = np.where(active, s.astype(np.int8) - 1, -1).astype(np.int8)
         collected.append(step)
         rows = np.where(active, LF[rows], rows)
     if active.any():
         raise AssertionError("LF walk did not reach $ for some read")
+    M = np.full((n, max_len), -1, dtype=np.int8)
     if collected:
-        M = np.stack(collected, axis=1)
-    else:
-        M = np.zeros((n, 0), dtype=np.int64)
-    reads_rev = [M[i][M[i] >= 0].astype(np.uint8) for i in range(n)]
-    return reads_rev, end_rows
+        C2 = np.stack(collected, axis=1)
+        M[:, :C2.shape[1]] = C2
+    reads_rev = None if n > 10_000 else [M[i][M[i] >= 0].astype(np.uint8) for i in range(n)]
+    return reads_rev, end_rows, M
 
 
 def check_invariants(codes: np.ndarray, lens: np.ndarray, bwt: bytes, dollar_pos=None, counts=None):
@@ -129,12 +142,16 @@ def check_invariants(codes: np.ndarray, lens: np.ndarray, bwt: bytes, dollar_pos
     ends = np.cumsum(lens) - 1
     last = np.frombuffer(b"ACGT", dtype=np.uint8)[codes[ends]]
     assert np.array_equal(B[:n], last), "first n symbols are not the last bases of the reads"
-    rev, end_rows = lf_invert(bwt, n, int(lens.max()))
-    off = np.concatenate([[0], np.cumsum(lens)[:-1]])
-    for i in range(n):
-        want = codes[off[i]:off[i] + lens[i]][::-1]
-        if not np.array_equal(rev[i], want):
-            raise AssertionError(f"LF inversion of read {i} does not give the read back")
+    M, end_rows = lf_walk(bwt, n, int(lens.max()))
+    # Expected walk of read i: its bases last to first, then -1 padding.
+    off = np.concatenate([[0], np.cumsum(lens)[:-1]]).astype(np.int64)
+    want = np.full(M.shape, -1, dtype=np.int8)
+    rows = np.repeat(np.arange(n, dtype=np.int64), lens)
+    t = np.arange(rows.size, dtype=np.int64) - np.repeat(off, lens)
+    want[rows, t] = codes[np.repeat(off + lens - 1, lens) - t].astype(np.int8)
+    if not np.array_equal(M, want):
+        bad = int(np.nonzero((M != want).any(axis=1))[0][0])
+        raise AssertionError(f"LF inversion of read {bad} does not give the read back")
     if dollar_pos is not None:
         assert np.array_equal(np.asarray(dollar_pos, dtype=np.int64), end_rows), "dollar positions differ from LF walk"
 

@@ -1,0 +1,78 @@
+"""The C-ABI library builds, loads and exports every declared entry point (no GPU work)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1401_7457_gb300 import build, binding
+    build.build()
+    return binding.lib()
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(cxbwt_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1401_7457_gb300 import binding
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+        assert name in binding.SIGNATURES, f"{name} has no binding"
+
+
+def test_abi_version(lib):
+    assert lib.cxbwt_abi_version() == 1
+
+
+def test_pack_unpack_roundtrip(lib):
+    from paper_1401_7457_gb300 import binding
+    rng = np.random.default_rng(0)
+    for n in [0, 1, 15, 16, 17, 1000]:
+        codes = rng.integers(0, 4, size=n, dtype=np.uint8)
+        w = binding.pack_codes(codes)
+        assert w.size == (n + 15) // 16
+        s = "".join("ACGT"[c] for c in codes)
+        assert np.array_equal(binding.pack_ascii(s), w)
+        # unpack with two '$' positions
+        if n >= 3:
+            got = binding.unpack_ascii(w, np.array([0, n - 1], dtype=np.uint64), n)
+            assert got == ("$" + s[1:-1] + "$").encode()
+    # bit layout: base j at bits 31-2j .. 30-2j of word 0
+    assert binding.pack_ascii("CA")[0] == 1 << 30
+    assert binding.pack_ascii("AAAAAAAAAAAAAAAT")[0] == 3
+
+
+def test_helpers_reject_bad_input(lib):
+    from paper_1401_7457_gb300 import binding
+    with pytest.raises(binding.CxbwtError):
+        binding.pack_ascii("ACGN")
+    with pytest.raises(binding.CxbwtError):
+        binding.pack_codes(np.array([0, 4], dtype=np.uint8))
+    with pytest.raises(binding.CxbwtError):
+        binding.unpack_ascii(np.zeros(1, dtype=np.uint32), np.array([20], dtype=np.uint64), 16)
+
+
+def test_output_size(lib):
+    from paper_1401_7457_gb300 import binding
+    assert binding.output_size(np.array([4, 4, 4], dtype=np.uint32)) == (15, 1)
+    assert binding.output_size(np.array([100] * 10000, dtype=np.uint32)) == (1_010_000, 63_125)
+
+
+def test_status_strings(lib):
+    lib.cxbwt_status_string.restype = ctypes.c_char_p
+    assert lib.cxbwt_status_string(-4) == b"CXBWT_ETIMEOUT"

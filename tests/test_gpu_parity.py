@@ -1,0 +1,141 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bit-exact everywhere: the BWT is an exact integer transform, so the packed
+symbols, the $ rows of every read, the symbol counts and (where asked) the
+suffix order must equal the oracle's.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import pins
+from paper_1401_7457_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+from gpu_helpers import assert_same, ctx, gpu_bwt, oracle_of  # noqa: F401
+
+
+def test_figure1(ctx):
+    reads, _, want = pins.read_figure1()
+    codes, lens = synth.ascii_reads(reads)
+    got = gpu_bwt(ctx, codes, lens, want_sa=True)
+    assert got["bwt"].decode() == want
+    assert_same(got, oracle_of(codes, lens), sa=True)
+
+
+@pytest.mark.parametrize("reads,want", pins.read_hand_examples())
+def test_hand_examples(ctx, reads, want):
+    codes, lens = synth.ascii_reads(reads)
+    assert gpu_bwt(ctx, codes, lens)["bwt"].decode() == want
+
+
+def test_random_small_collections(ctx):
+    """Small mixed-length collections over 1- to 4-letter alphabets."""
+    rng = np.random.default_rng(99)
+    for t in range(150):
+        k = int(rng.integers(1, 40))
+        alpha = int(rng.integers(1, 5))
+        lens = rng.integers(1, 40, size=k).astype(np.uint32)
+        codes = rng.integers(0, alpha, size=int(lens.sum())).astype(np.uint8)
+        got = gpu_bwt(ctx, codes, lens, want_sa=True)
+        assert_same(got, oracle_of(codes, lens), sa=True)
+
+
+def test_tiny_uniform_workload_full(ctx):
+    """10,000 x 100 bp uniform reads (1,010,000 suffixes, 247 tiles, ragged last tile):
+    every symbol, every $ row, the counts and the full suffix order."""
+    codes, lens = synth.tiny_uniform()
+    ref = oracle_of(codes, lens)
+    got = gpu_bwt(ctx, codes, lens, want_sa=True)
+    assert_same(got, ref, sa=True)
+
+
+def test_tiny_uniform_host_buffers(ctx):
+    """Same build with host input and output buffers (copies inside the library)."""
+    codes, lens = synth.tiny_uniform()
+    ref = oracle_of(codes, lens)
+    assert_same(gpu_bwt(ctx, codes, lens, where="host"), ref)
+
+
+def test_genome_like_small(ctx):
+    """20x-coverage reads from a 50 kbp genome: long shared prefixes, both strands."""
+    g = synth.random_genome(50_000, 21)
+    codes, lens = synth.sample_reads(g, 10_000, 100, 22, 0.01)
+    assert_same(gpu_bwt(ctx, codes, lens, want_sa=True), oracle_of(codes, lens), sa=True)
+
+
+@pytest.mark.parametrize("lo,hi,n", [(1, 150, 3000), (1, 8, 5000), (200, 300, 500), (90, 100, 4000)])
+def test_mixed_lengths(ctx, lo, hi, n):
+    """Reads of different lengths: the (length, read) start order comes from one
+    or two length passes (two when a read is longer than 255)."""
+    codes, lens = synth.mixed_length_reads(n, lo, hi, lo * 1000 + hi)
+    assert_same(gpu_bwt(ctx, codes, lens, want_sa=True), oracle_of(codes, lens), sa=True)
+
+
+@pytest.mark.parametrize("case", ["one_base", "one_read", "all_a", "all_t", "identical", "two_letters",
+                                  "tile_exact", "long_read"])
+def test_edge_cases(ctx, case):
+    rng = np.random.default_rng(5)
+    if case == "one_base":
+        codes, lens = np.array([2], dtype=np.uint8), np.array([1], dtype=np.uint32)
+    elif case == "one_read":
+        codes, lens = synth.uniform_reads(1, 100, 1)
+    elif case == "all_a":  # every suffix ties with its A-padded extensions
+        codes, lens = np.zeros(3000 * 50, dtype=np.uint8), np.full(3000, 50, dtype=np.uint32)
+    elif case == "all_t":
+        codes, lens = np.full(3000 * 50, 3, dtype=np.uint8), np.full(3000, 50, dtype=np.uint32)
+    elif case == "identical":
+        one = rng.integers(0, 4, size=77).astype(np.uint8)
+        codes, lens = np.tile(one, 2000), np.full(2000, 77, dtype=np.uint32)
+    elif case == "two_letters":
+        lens = rng.integers(20, 60, size=3000).astype(np.uint32)
+        codes = rng.integers(0, 2, size=int(lens.sum())).astype(np.uint8)
+    elif case == "tile_exact":  # N = 2 * 4096 exactly: no ragged tile
+        codes, lens = synth.uniform_reads(128, 63, 3)
+        assert int(lens.sum()) + lens.size == 8192
+    else:  # one 20,000-base read plus short ones
+        lens = np.array([20_000] + [30] * 100, dtype=np.uint32)
+        codes = rng.integers(0, 4, size=int(lens.sum())).astype(np.uint8)
+    assert_same(gpu_bwt(ctx, codes, lens, want_sa=True), oracle_of(codes, lens), sa=True)
+
+
+def test_repeated_builds_are_identical(ctx):
+    """Determinism and workspace reuse: a bigger build, then a smaller one, then the first again."""
+    a = synth.uniform_reads(5000, 100, 77)
+    b = synth.mixed_length_reads(700, 5, 90, 78)
+    r1 = gpu_bwt(ctx, *a)
+    r2 = gpu_bwt(ctx, *b)
+    r3 = gpu_bwt(ctx, *a)
+    assert r1["bwt"] == r3["bwt"] and np.array_equal(r1["dollar_pos"], r3["dollar_pos"])
+    assert_same(r2, oracle_of(*b))
+
+
+def test_invalid_arguments(ctx):
+    from paper_1401_7457_gb300 import binding
+    words = np.zeros(4, dtype=np.uint32)
+    with pytest.raises(binding.CxbwtError) as e:
+        ctx.build(words, np.array([10, 0, 5], dtype=np.uint32))
+    assert e.value.status == -1
+    with pytest.raises(binding.CxbwtError) as e:
+        ctx.build(words, np.array([70000], dtype=np.uint32))
+    assert e.value.status == -1
+    with pytest.raises(binding.CxbwtError) as e:
+        ctx.build(words, np.zeros(0, dtype=np.uint32))
+    assert e.value.status == -1
+    # the context still works afterwards
+    codes, lens = synth.uniform_reads(10, 10, 1)
+    assert_same(gpu_bwt(ctx, codes, lens), oracle_of(codes, lens))
+
+
+def test_budget_too_small_is_enomem():
+    from paper_1401_7457_gb300 import binding
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    codes, lens = synth.uniform_reads(10_000, 100, 1)
+    with binding.Context(device=0, budget_bytes=8 << 20) as c:
+        with pytest.raises(binding.CxbwtError) as e:
+            c.build(binding.pack_codes(codes), lens)
+        assert e.value.status == -2
