@@ -38,8 +38,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "BWT build Gbases/s at 1 GB300 (% HBM roofline); served p50/p99 vs plain loop"
 UNIT = "Gbase/s"
-WORKLOAD = ("genome-like: 1,000,000 reads x 100 bp from both strands of a seeded 5 Mbp uniform genome "
-            "(20x coverage), 1% substitutions, seed 2; 101,000,000 suffixes")
+WORKLOAD = ("genome-like: {n:,} reads x 100 bp from both strands of a seeded 5 Mbp uniform genome "
+            "(1M reads = 20x coverage), 1% substitutions, seed 2; {N:,} suffixes")
 SORT_BYTES_PER_ITEM = 16  # algorithmic bytes per suffix per digit pass: 4 B key + 4 B id, read and written
 PROFILE = os.path.join(ROOT, "profiles", "onesweep_digit_pass_genome_like.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_1401_7457_gb300", "csrc", "k_sort.cu")
@@ -167,7 +167,7 @@ def run_reference(args, rank, world):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "data": "synthetic", "config": {"workload": WORKLOAD.format(n=lens.size, N=int(lens.sum()) + lens.size)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -180,8 +180,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cxbwt", choices=["cxbwt", "reference"])
-    ap.add_argument("--cpu-sample-reads", type=int, default=300_000)
+    ap.add_argument("--cpu-sample-reads", type=int, default=500_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--reads", type=int, default=1_000_000,
+                    help="reads per GPU (default: the 1M-read workload; smaller only for profiling captures)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -200,7 +202,7 @@ def main():
 
     # Each rank builds its own independent collection (weak scaling, no data-path collective).
     seed = 2 if rank == 0 else synth.derive_seed(2, rank)
-    codes, lens = synth.genome_like(seed=seed)
+    codes, lens = synth.genome_like(seed=seed, n_reads=args.reads)
     words = binding.pack_codes(codes)
     n = lens.size
     bases = int(lens.sum())
@@ -304,7 +306,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n_reads": n, "read_len": int(lens[0]), "bases_per_gpu": bases,
+                "config": {"workload": WORKLOAD.format(n=n, N=N), "n_reads": n, "read_len": int(lens[0]), "bases_per_gpu": bases,
                            "suffixes_per_gpu": N, "l2": "flushed between steps (512 MB write outside the events)",
                            "input": "device-resident (HBM) before the timed region; outputs left in HBM"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
