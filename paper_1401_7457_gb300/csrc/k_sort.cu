@@ -53,8 +53,8 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t x, uint32_
   return warp_prefix + incl - x;
 }
 
-template <int THREADS, int IPT, int MODE, bool WRITE_KEY>
-__global__ void __launch_bounds__(THREADS) k_onesweep(const PassArgs a) {
+template <int THREADS, int IPT, int MIN_BLOCKS, int MODE, bool WRITE_KEY>
+__global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs a) {
   constexpr int TILE = THREADS * IPT;
   constexpr int WARPS = THREADS / 32;
   static_assert(THREADS >= 256 && THREADS % 32 == 0, "one thread per digit value is needed");
@@ -62,9 +62,10 @@ __global__ void __launch_bounds__(THREADS) k_onesweep(const PassArgs a) {
   extern __shared__ __align__(16) uint32_t s_stage[];  // keys [TILE], then values [TILE]
   uint32_t* s_keys = s_stage;
   uint32_t* s_vals = s_stage + TILE;
-  __shared__ uint32_t s_whist[WARPS][kRadix];  // per-warp digit counts, then per-warp offsets
-  __shared__ uint32_t s_dexcl[kRadix];         // tile-local first row of each digit
-  __shared__ uint32_t s_gbase[kRadix];         // global row of tile-local row 0 of each digit
+  // Per-warp digit counts; after the look-back, the tile-local row of the
+  // warp's first item of each digit.
+  __shared__ uint32_t s_whist[WARPS][kRadix];
+  __shared__ uint32_t s_gbase[kRadix];  // global row of tile-local row 0 of each digit
   __shared__ uint32_t s_scan[8];
   __shared__ uint32_t s_tile;
 
@@ -78,34 +79,35 @@ __global__ void __launch_bounds__(THREADS) k_onesweep(const PassArgs a) {
   }
   __syncthreads();
   const uint32_t tile = s_tile;
-  const uint64_t tile_base = uint64_t(tile) * TILE;
-  const uint64_t warp_base = tile_base + uint64_t(warp) * 32 * IPT;
+  const uint32_t tile_base = tile * uint32_t(TILE);  // n_items < 2^32
+  const uint32_t warp_base = tile_base + uint32_t(warp) * 32u * IPT + lane;
+  const uint32_t n_items = a.n_items;
 
-  uint32_t key[IPT], val[IPT], digit[IPT], rank[IPT];
+  uint32_t key[IPT], val[IPT], digit[IPT];
 
   // ---- 2. load ------------------------------------------------------------
   if (MODE == kSrcInitUniform) {
+    const uint32_t L = a.R.uniform_len;
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
-      const uint64_t idx = warp_base + j * 32 + lane;
-      const uint32_t L = a.R.uniform_len;
+      const uint32_t idx = warp_base + j * 32;
       // Position idx of the (suffix length, read) order: length idx / n, read idx % n.
-      const uint32_t slen = uint32_t(idx / a.n_reads);
-      const uint32_t i = uint32_t(idx - uint64_t(slen) * a.n_reads);
+      const uint32_t slen = idx / a.n_reads;
+      const uint32_t i = idx - slen * a.n_reads;
       val[j] = (i << a.R.shift) | (L - min(slen, L));
     }
   } else {
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
-      const uint64_t idx = warp_base + j * 32 + lane;
-      val[j] = idx < a.n_items ? __ldg(a.vals_in + idx) : 0u;
+      const uint32_t idx = warp_base + j * 32;
+      val[j] = idx < n_items ? __ldg(a.vals_in + idx) : 0u;
     }
   }
   if (MODE == kSrcCarried) {
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
-      const uint64_t idx = warp_base + j * 32 + lane;
-      key[j] = idx < a.n_items ? __ldg(a.keys_in + idx) : 0u;
+      const uint32_t idx = warp_base + j * 32;
+      key[j] = idx < n_items ? __ldg(a.keys_in + idx) : 0u;
     }
   } else if (MODE == kSrcLength) {
 #pragma unroll
@@ -116,18 +118,19 @@ __global__ void __launch_bounds__(THREADS) k_onesweep(const PassArgs a) {
   } else {
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
-      const uint64_t idx = warp_base + j * 32 + lane;
-      key[j] = idx < a.n_items ? window16(a.R, decode(a.R, val[j]), a.window_c0) : 0u;
+      const uint32_t idx = warp_base + j * 32;
+      key[j] = idx < n_items ? window16(a.R, decode(a.R, val[j]), a.window_c0) : 0u;
     }
   }
 #pragma unroll
   for (int j = 0; j < IPT; ++j) {
-    const uint64_t idx = warp_base + j * 32 + lane;
+    const uint32_t idx = warp_base + j * 32;
     // Items past the end get a value no digit has, so they match only each other.
-    digit[j] = idx < a.n_items ? ((key[j] >> a.key_shift) & (kRadix - 1)) : uint32_t(kRadix);
+    digit[j] = idx < n_items ? ((key[j] >> a.key_shift) & (kRadix - 1)) : uint32_t(kRadix);
   }
 
   // ---- 3. stable rank inside the warp, in item order ------------------------
+  // digit[j] becomes (rank of the item among the warp's items of its digit) << 9 | digit.
   const uint32_t lt = lanemask_lt();
 #pragma unroll
   for (int j = 0; j < IPT; ++j) {
@@ -140,7 +143,7 @@ __global__ void __launch_bounds__(THREADS) k_onesweep(const PassArgs a) {
       s_whist[warp][d] = prior + __popc(peers);
     }
     prior = __shfl_sync(0xFFFFFFFFu, prior, leader);
-    rank[j] = prior + __popc(peers & lt);
+    digit[j] = ((prior + __popc(peers & lt)) << 9) | d;
     __syncwarp();
   }
   __syncthreads();
@@ -162,18 +165,21 @@ __global__ void __launch_bounds__(THREADS) k_onesweep(const PassArgs a) {
   }
   const uint32_t local_excl = block_exclusive_scan_256<THREADS>(tile_cnt, s_scan);
   if (tid < kRadix) {
-    s_dexcl[tid] = local_excl;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) s_whist[w][tid] += local_excl;
     uint32_t before = 0;  // items with this digit in tiles 0 .. tile-1
     if (tile > 0) {
       const uint32_t agg = 2u * a.epoch, pre = 2u * a.epoch + 1u;
-      int64_t p = int64_t(tile) - 1;
+      uint32_t p = tile - 1;
       uint64_t t0 = 0;
       uint32_t spins = 0;
-      while (p >= 0) {
+      while (true) {
         const unsigned long long s = load_relaxed_u64(a.status + uint64_t(p) * kRadix + tid);
         const uint32_t flag = uint32_t(s >> 32);
         if (flag != agg && flag != pre) {  // not yet published in this pass
-          if ((++spins & 63u) == 0u) {
+          ++spins;
+          if (spins > 4) __nanosleep(64);
+          if ((spins & 63u) == 0u) {
             const uint64_t now = global_timer_ns();
             if (t0 == 0) {
               t0 = now;
@@ -185,7 +191,7 @@ __global__ void __launch_bounds__(THREADS) k_onesweep(const PassArgs a) {
           continue;
         }
         before += uint32_t(s);
-        if (flag == pre) break;
+        if (flag == pre || p == 0) break;
         --p;
       }
       store_relaxed_u64(a.status + uint64_t(tile) * kRadix + tid,
@@ -198,16 +204,16 @@ __global__ void __launch_bounds__(THREADS) k_onesweep(const PassArgs a) {
   // ---- 5. stage sorted in shared memory, write out --------------------------
 #pragma unroll
   for (int j = 0; j < IPT; ++j) {
-    const uint32_t d = digit[j];
+    const uint32_t d = digit[j] & 0x1FFu;
     if (d < kRadix) {
-      const uint32_t r = s_dexcl[d] + s_whist[warp][d] + rank[j];
+      const uint32_t r = s_whist[warp][d] + (digit[j] >> 9);
       s_keys[r] = key[j];
       s_vals[r] = val[j];
     }
   }
   __syncthreads();
-  const uint64_t left = uint64_t(a.n_items) - tile_base;
-  const uint32_t n_valid = left < uint64_t(TILE) ? uint32_t(left) : uint32_t(TILE);
+  const uint32_t left = n_items - tile_base;
+  const uint32_t n_valid = left < uint32_t(TILE) ? left : uint32_t(TILE);
 #pragma unroll
   for (int j = 0; j < IPT; ++j) {
     const uint32_t r = j * THREADS + tid;
@@ -215,7 +221,7 @@ __global__ void __launch_bounds__(THREADS) k_onesweep(const PassArgs a) {
       const uint32_t k = s_keys[r];
       const uint32_t d = (k >> a.key_shift) & (kRadix - 1);
       const uint32_t g = s_gbase[d] + r;
-      if (g < a.n_items) {
+      if (g < n_items) {
         a.vals_out[g] = s_vals[r];
         if (WRITE_KEY) a.keys_out[g] = k;
       } else {
@@ -225,38 +231,65 @@ __global__ void __launch_bounds__(THREADS) k_onesweep(const PassArgs a) {
   }
 }
 
-constexpr int kThreads = 256;
-constexpr int kIpt = 16;
+// Tile shapes compiled in (threads, items per thread, CTAs per SM the register
+// budget is sized for).
+template <int T, int I, int B>
+struct Shape {
+  static constexpr int threads = T, ipt = I, min_blocks = B;
+};
 
-template <int MODE, bool WK>
-cudaError_t launch_mode(const PassArgs& a, const TileShape& s, cudaStream_t st) {
-  const size_t smem = onesweep_smem_bytes(s);
-  auto kern = k_onesweep<kThreads, kIpt, MODE, WK>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
-  kern<<<a.n_tiles, kThreads, smem, st>>>(a);
+template <class S, int MODE, bool WK>
+cudaError_t launch_mode(const PassArgs& a, cudaStream_t st) {
+  const size_t smem = size_t(S::threads) * S::ipt * 2 * sizeof(uint32_t);
+  auto kern = k_onesweep<S::threads, S::ipt, S::min_blocks, MODE, WK>;
+  static bool configured = false;  // per instantiation; attributes are per function
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  kern<<<a.n_tiles, S::threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
+template <class S>
+cudaError_t launch_shape(const PassArgs& a, int mode, bool write_key, cudaStream_t st) {
+  switch (mode) {
+    case kSrcInitUniform: return write_key ? launch_mode<S, kSrcInitUniform, true>(a, st)
+                                           : launch_mode<S, kSrcInitUniform, false>(a, st);
+    case kSrcExtract: return write_key ? launch_mode<S, kSrcExtract, true>(a, st)
+                                       : launch_mode<S, kSrcExtract, false>(a, st);
+    case kSrcCarried: return write_key ? launch_mode<S, kSrcCarried, true>(a, st)
+                                       : launch_mode<S, kSrcCarried, false>(a, st);
+    case kSrcLength: return write_key ? launch_mode<S, kSrcLength, true>(a, st)
+                                      : launch_mode<S, kSrcLength, false>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+using ShapeSmall = Shape<256, 8, 6>;    // 2048 items
+using ShapeMid = Shape<256, 16, 4>;     // 4096 items
+using ShapeLarge = Shape<512, 16, 2>;   // 8192 items
+
 }  // namespace
 
-TileShape onesweep_shape(int /*tile_items_hint*/) { return TileShape{kThreads, kIpt}; }
+TileShape onesweep_shape(int tile_items_hint) {
+  if (tile_items_hint == 2048) return TileShape{ShapeSmall::threads, ShapeSmall::ipt};
+  if (tile_items_hint == 8192) return TileShape{ShapeLarge::threads, ShapeLarge::ipt};
+  return TileShape{ShapeMid::threads, ShapeMid::ipt};
+}
 
 size_t onesweep_smem_bytes(const TileShape& s) { return size_t(s.tile()) * 2 * sizeof(uint32_t); }
 
 cudaError_t launch_onesweep(const PassArgs& a, int mode, bool write_key, const TileShape& s, cudaStream_t st) {
   if (a.n_tiles == 0) return cudaSuccess;
-  switch (mode) {
-    case kSrcInitUniform: return write_key ? launch_mode<kSrcInitUniform, true>(a, s, st)
-                                           : launch_mode<kSrcInitUniform, false>(a, s, st);
-    case kSrcExtract: return write_key ? launch_mode<kSrcExtract, true>(a, s, st)
-                                       : launch_mode<kSrcExtract, false>(a, s, st);
-    case kSrcCarried: return write_key ? launch_mode<kSrcCarried, true>(a, s, st)
-                                       : launch_mode<kSrcCarried, false>(a, s, st);
-    case kSrcLength: return write_key ? launch_mode<kSrcLength, true>(a, s, st)
-                                      : launch_mode<kSrcLength, false>(a, s, st);
-    default: return cudaErrorInvalidValue;
-  }
+  if (s.threads == ShapeSmall::threads && s.items_per_thread == ShapeSmall::ipt)
+    return launch_shape<ShapeSmall>(a, mode, write_key, st);
+  if (s.threads == ShapeLarge::threads && s.items_per_thread == ShapeLarge::ipt)
+    return launch_shape<ShapeLarge>(a, mode, write_key, st);
+  return launch_shape<ShapeMid>(a, mode, write_key, st);
 }
 
 }  // namespace cxbwt

@@ -139,3 +139,15 @@ def test_budget_too_small_is_enomem():
         with pytest.raises(binding.CxbwtError) as e:
             c.build(binding.pack_codes(codes), lens)
         assert e.value.status == -2
+
+
+@pytest.mark.parametrize("tile_items", [2048, 4096, 8192])
+def test_tile_shapes_identical(tile_items):
+    """The result does not depend on the tile shape of the digit passes."""
+    from paper_1401_7457_gb300 import binding
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    codes, lens = synth.mixed_length_reads(20_000, 30, 120, 31)
+    ref = oracle_of(codes, lens)
+    with binding.Context(device=0, tile_items=tile_items) as c:
+        assert_same(gpu_bwt(c, codes, lens), ref)
