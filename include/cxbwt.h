@@ -80,8 +80,20 @@ typedef struct {
   int tile_items;               /* items per radix tile; 0 = automatic */
   int async;                    /* nonzero: calls return after enqueue when outputs are on the device */
   int timing;                   /* nonzero: record CUDA events around every phase (see cxbwt_stats) */
-  int reserved[8];
+  int algorithm;                /* CXBWT_ALGO_*: how the suffixes are sorted (all give identical output) */
+  int reserved[7];
 } cxbwt_options;
+
+/* Sort plans.  Every plan computes the same B_R; they differ in speed only.
+ *  AUTO     - GROUPS when the reads are at most 272 bases, else LSD.
+ *  LSD      - stable LSD radix passes over every 4-base digit of the
+ *             A-padded suffixes (Section 3.2 as stated: one pass per digit).
+ *  GROUPS   - LSD passes over the first 16 bases only (the l-prefix
+ *             partition of Section 3.1 with l = 16), then each group of
+ *             suffixes sharing those bases is finished on chip. */
+#define CXBWT_ALGO_AUTO 0
+#define CXBWT_ALGO_LSD 1
+#define CXBWT_ALGO_GROUPS 2
 
 /* Counters accumulated by a context since creation or cxbwt_reset_stats. */
 typedef struct {

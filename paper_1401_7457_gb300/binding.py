@@ -33,7 +33,7 @@ class CxbwtError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("device_budget_bytes", ctypes.c_uint64), ("device", ctypes.c_int), ("prefix_len", ctypes.c_int),
                 ("digit_bits", ctypes.c_int), ("tile_items", ctypes.c_int), ("async_", ctypes.c_int),
-                ("timing", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+                ("timing", ctypes.c_int), ("algorithm", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
 
 
 class Stats(ctypes.Structure):
@@ -166,8 +166,10 @@ def _to_numpy(x):
 class Context:
     """One cxbwt context (device workspace + bookkeeping) on one device."""
 
+    ALGO_AUTO, ALGO_LSD, ALGO_GROUPS = 0, 1, 2
+
     def __init__(self, device: int = 0, budget_bytes: int = 0, async_: bool = False, timing: bool = False,
-                 tile_items: int = 0):
+                 tile_items: int = 0, algorithm: int = 0):
         L = lib()
         opt = Options()
         L.cxbwt_default_options(ctypes.byref(opt))
@@ -176,6 +178,7 @@ class Context:
         opt.async_ = 1 if async_ else 0
         opt.timing = 1 if timing else 0
         opt.tile_items = tile_items
+        opt.algorithm = algorithm
         h = ctypes.c_void_p()
         st = L.cxbwt_create(ctypes.byref(h), ctypes.byref(opt))
         if st != 0:

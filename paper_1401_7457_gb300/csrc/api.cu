@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "../../include/cxbwt.h"
+#include "group.cuh"
 #include "kernels.cuh"
 
 using namespace cxbwt;
@@ -48,7 +49,7 @@ struct cxbwt_ctx {
   uint64_t held = 0;
   std::string err;
 
-  DevBuf vals[2], keys[2], status, P, base, lenhist, desc, misc, store, out_bwt, out_dollar, out_sa;
+  DevBuf vals[2], keys[2], status, P, base, lenhist, desc, misc, store, out_bwt, out_dollar, out_sa, seglist, rhist;
   uint32_t epoch = 0;
   unsigned long long* h_small = nullptr;  // pinned: device error word, length stats
   cudaStream_t last_stream = nullptr;
@@ -130,6 +131,7 @@ constexpr size_t kMiscTileCounter = 0;   // uint32
 constexpr size_t kMiscErr = 4;           // uint32
 constexpr size_t kMiscCounts = 64;       // 5 x uint64
 constexpr size_t kMiscLenStats = 128;    // 4 x uint64
+constexpr size_t kMiscSeg = 192;         // 4 x uint32: group-finish list lengths and work counter
 constexpr size_t kMiscBytes = 256;
 
 uint32_t bits_for(uint32_t x) {  // smallest s with 2^s > x
@@ -229,6 +231,21 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   pl.W = (pl.Lmax + 15) / 16;
   pl.len_passes = pl.uniform ? 0 : (pl.Lmax > 255 ? 2 : 1);
   pl.n_words = (sum + 15) / 16;
+  const int seg_words = segsort_words(pl.Lmax);
+  bool groups;
+  switch (c->opt.algorithm) {
+    case CXBWT_ALGO_LSD: groups = false; break;
+    case CXBWT_ALGO_GROUPS:
+      if (!seg_words) return fail(c, CXBWT_EUNSUPPORTED, "the group plan handles reads of at most 272 bases");
+      groups = true;
+      break;
+    case CXBWT_ALGO_AUTO: groups = seg_words != 0; break;
+    default: return fail(c, CXBWT_EINVAL, "unknown algorithm %d", c->opt.algorithm);
+  }
+  // Windows [0, w_last] are sorted by LSD passes over all rows; with the
+  // group plan only window 0 is, and the groups are finished on chip.
+  const uint32_t w_last = groups ? 0u : pl.W - 1;
+  const uint32_t d_sorted = std::min<uint32_t>(pl.D, 4 * (w_last + 1));
   const uint64_t max_value = ((n - 1) << pl.shift) | pl.Lmax;
   if (pl.shift > 31 || ((n - 1) >> (32 - pl.shift)) != 0 || max_value > 0xFFFFFFFFull)
     return fail(c, CXBWT_EUNSUPPORTED, "n_reads x 2^%u exceeds the 32-bit suffix id space of one sort", pl.shift);
@@ -325,7 +342,7 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
 
   // ---- 1. all-digit histogram -----------------------------------------------
   CX_CUDA(c, launch_poscount(R, uint32_t(n), pl.Lmax, static_cast<uint32_t*>(c->P.p), c->sm_count, st));
-  CX_CUDA(c, launch_digitbase(static_cast<const uint32_t*>(c->P.p), pl.Lmax, pl.D, pl.uniform ? 1 : 0,
+  CX_CUDA(c, launch_digitbase(static_cast<const uint32_t*>(c->P.p), pl.Lmax, d_sorted, pl.uniform ? 1 : 0,
                               uint32_t(n), pl.Lmax, d_lenhist, d_base, st));
   launches += 2;
 
@@ -349,7 +366,7 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
     ++launches;
   }
   if (timing) CX_CUDA(c, cudaEventRecord(c->ev[1], st));
-  uint64_t sort_launches = 0;
+  uint64_t sort_launches = 0, sort_items = 0;
   for (uint32_t j = 0; j < pl.len_passes; ++j) {
     a.vals_in = vals[cur];
     a.vals_out = vals[cur ^ 1];
@@ -362,16 +379,18 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
     CX_CUDA(c, launch_onesweep(a, kSrcLength, false, shape, st));
     cur ^= 1;
     ++sort_launches;
+    sort_items += pl.N;
   }
   bool first = pl.uniform;
-  for (int64_t w = int64_t(pl.W) - 1; w >= 0; --w) {
+  for (int64_t w = int64_t(w_last); w >= 0; --w) {
     const uint32_t d_lo = uint32_t(4 * w);
     const uint32_t d_hi = std::min<uint32_t>(d_lo + 3, pl.D - 1);
     for (int64_t d = d_hi; d >= int64_t(d_lo); --d) {
       const bool first_in_window = (uint32_t(d) == d_hi);
       const bool last_in_window = (uint32_t(d) == d_lo);
       const int mode = first_in_window ? (first ? kSrcInitUniform : kSrcExtract) : kSrcCarried;
-      const bool write_key = !last_in_window;
+      // The group plan keeps the window-0 keys of the final order: groups are runs of equal keys.
+      const bool write_key = !last_in_window || groups;
       a.vals_in = vals[cur];
       a.vals_out = vals[cur ^ 1];
       a.keys_in = (mode == kSrcCarried) ? keys[kin] : nullptr;
@@ -386,10 +405,85 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
       if (write_key) kin = kout;
       first = false;
       ++sort_launches;
+      sort_items += pl.N;
     }
   }
   if (timing) CX_CUDA(c, cudaEventRecord(c->ev[2], st));
   launches += sort_launches;
+
+  // ---- 3b. group plan: finish every group of equal first windows on chip ------
+  if (groups && pl.Lmax > 16) {
+    const uint64_t cta_cap = pl.N / 33 + 1, big_cap = pl.N / kCtaMax + 1;
+    CX_TRY(ensure(c, c->seglist, (cta_cap + big_cap) * 8, "group lists"));
+    auto* d_seg = reinterpret_cast<uint32_t*>(misc + kMiscSeg);
+    CX_CUDA(c, cudaMemsetAsync(d_seg, 0, 16, st));
+    SegArgs g{};
+    g.keys = keys[kin];
+    g.vals = vals[cur];
+    g.n_items = uint32_t(pl.N);
+    g.R = R;
+    g.depth = 16;
+    g.cta_list = static_cast<uint2*>(c->seglist.p);
+    g.cta_cap = uint32_t(cta_cap);
+    g.big_list = g.cta_list + cta_cap;
+    g.big_cap = uint32_t(big_cap);
+    g.counts = d_seg;
+    g.err = d_err;
+    CX_CUDA(c, launch_segsort(g, seg_words, c->sm_count, st));
+    launches += 2;
+    // Remainders too large for one CTA (rare: long runs of equal bases) are
+    // finished here with LSD passes over bases 16.. restricted to their rows.
+    CX_CUDA(c, cudaMemcpyAsync(c->h_small + 5, d_seg, 8, cudaMemcpyDeviceToHost, st));
+    CX_CUDA(c, cudaStreamSynchronize(st));
+    const uint32_t n_big = std::min<uint32_t>(reinterpret_cast<const uint32_t*>(c->h_small + 5)[1], g.big_cap);
+    if (n_big) {
+      std::vector<uint2> big(n_big);
+      CX_CUDA(c, cudaMemcpyAsync(big.data(), g.big_list, n_big * 8, cudaMemcpyDeviceToHost, st));
+      CX_CUDA(c, cudaStreamSynchronize(st));
+      d2h += n_big * 8;
+      const uint32_t n_win = pl.W - 1;
+      CX_TRY(ensure(c, c->rhist, size_t(n_win) * 4 * kRadix * 4, "group digit counts"));
+      auto* rh = static_cast<uint32_t*>(c->rhist.p);
+      for (const uint2& bg : big) {
+        const uint32_t s0 = bg.x, m = bg.y;
+        CX_CUDA(c, cudaMemsetAsync(rh, 0, size_t(n_win) * 4 * kRadix * 4, st));
+        CX_CUDA(c, launch_range_hist(vals[cur] + s0, m, R, n_win, rh, c->sm_count, st));
+        launches += 2;
+        uint32_t* gv[2] = {vals[cur] + s0, vals[cur ^ 1] + s0};
+        uint32_t* gk[2] = {keys[0] + s0, keys[1] + s0};
+        int gc = 0, gki = 0;
+        PassArgs b = a;
+        b.n_items = m;
+        b.n_tiles = uint32_t((m + TILE - 1) / TILE);
+        for (uint32_t w = pl.W - 1; w >= 1; --w) {
+          const uint32_t d_lo = 4 * w;
+          const uint32_t d_hi = std::min<uint32_t>(d_lo + 3, pl.D - 1);
+          for (int64_t d = d_hi; d >= int64_t(d_lo); --d) {
+            const bool first_in_window = (uint32_t(d) == d_hi);
+            const bool last_in_window = (uint32_t(d) == d_lo);
+            const int mode = first_in_window ? kSrcExtract : kSrcCarried;
+            const bool write_key = !last_in_window;
+            b.vals_in = gv[gc];
+            b.vals_out = gv[gc ^ 1];
+            b.keys_in = (mode == kSrcCarried) ? gk[gki] : nullptr;
+            const int kout = (mode == kSrcCarried) ? (gki ^ 1) : gki;
+            b.keys_out = write_key ? gk[kout] : nullptr;
+            b.digit_base = rh + size_t((w - 1) * 4 + (uint32_t(d) - d_lo)) * kRadix;
+            b.key_shift = 24u - 8u * (uint32_t(d) - d_lo);
+            b.window_c0 = 16 * w;
+            b.epoch = ++c->epoch;
+            CX_CUDA(c, launch_onesweep(b, mode, write_key, shape, st));
+            gc ^= 1;
+            if (write_key) gki = kout;
+            ++launches;
+            ++sort_launches;
+            sort_items += m;
+          }
+        }
+        if (gc) CX_CUDA(c, cudaMemcpyAsync(gv[0], gv[1], size_t(m) * 4, cudaMemcpyDeviceToDevice, st));
+      }
+    }
+  }
 
   // ---- 4. emission -----------------------------------------------------------
   const uint64_t bwt_words = (pl.N + 15) / 16;
@@ -433,7 +527,7 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
 
   c->stats.kernel_launches += launches;
   c->stats.sort_pass_launches += sort_launches;
-  c->stats.sort_pass_items += sort_launches * pl.N;
+  c->stats.sort_pass_items += sort_items;
   c->stats.h2d_bytes += h2d;
   c->stats.d2h_bytes += d2h;
   c->stats.device_bytes_held = c->held;
@@ -530,7 +624,8 @@ void cxbwt_destroy(cxbwt_ctx* c) {
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   DevBuf* bufs[] = {&c->vals[0], &c->vals[1], &c->keys[0], &c->keys[1], &c->status, &c->P, &c->base,
-                    &c->lenhist, &c->desc, &c->misc, &c->store, &c->out_bwt, &c->out_dollar, &c->out_sa};
+                    &c->lenhist, &c->desc, &c->misc, &c->store, &c->out_bwt, &c->out_dollar, &c->out_sa,
+                    &c->seglist, &c->rhist};
   for (DevBuf* b : bufs) release(c, *b);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);

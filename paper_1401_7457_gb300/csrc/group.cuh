@@ -1,0 +1,33 @@
+// Launchers of the group-finishing kernels (k_group.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace cxbwt {
+
+constexpr uint32_t kCtaMax = 2048;  // largest group remainder finished by one CTA
+
+struct SegArgs {
+  const uint32_t* keys;   // first 16-base window of each row, ascending
+  uint32_t* vals;         // suffix ids, sorted by that window; finished in place
+  uint32_t n_items;
+  ReadIndex R;
+  uint32_t depth;         // bases already sorted (16)
+  uint2* cta_list;        // (first row, rows) of remainders of 33 .. kCtaMax rows
+  uint32_t cta_cap;
+  uint2* big_list;        // remainders of more rows, finished by the host
+  uint32_t big_cap;
+  uint32_t* counts;       // [0] cta_list length, [1] big_list length, [2] CTA work counter (zero on entry)
+  uint32_t* err;
+};
+
+// Key words a group remainder is sorted by for reads of at most max_len bases
+// (a compiled width >= ceil((max_len - 16) / 16)), or 0 if too long.
+int segsort_words(uint32_t max_len);
+cudaError_t launch_segsort(const SegArgs& a, int nw, int sm_count, cudaStream_t st);
+// Digit bases (exclusive, per digit position) of windows 1 .. n_win over n rows of vals.
+cudaError_t launch_range_hist(const uint32_t* vals, uint32_t n, const ReadIndex& R, uint32_t n_win, uint32_t* hist,
+                              int sm_count, cudaStream_t st);
+
+}  // namespace cxbwt

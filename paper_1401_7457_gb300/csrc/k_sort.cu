@@ -13,9 +13,9 @@
 //   1. take a tile id from an atomic counter (so every lower tile is already
 //      running: the look-back below always makes progress),
 //   2. load the tile (warp-striped, coalesced) and compute each item's digit,
-//   3. rank items inside the tile: warp-level __match_any_sync groups equal
-//      digits; a per-warp shared-memory histogram accumulates counts in item
-//      order, so the ranking is stable,
+//   3. rank items inside the tile: warp-level ballots (one per digit bit)
+//      group equal digits; a per-warp shared-memory histogram accumulates
+//      counts in item order, so the ranking is stable,
 //   4. publish the tile's per-digit counts, then walk back over the
 //      predecessors' published counts (decoupled look-back) to find, for each
 //      digit, how many items of earlier tiles precede this tile; the first row
@@ -130,12 +130,27 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
   }
 
   // ---- 3. stable rank inside the warp, in item order ------------------------
-  // digit[j] becomes (rank of the item among the warp's items of its digit) << 9 | digit.
+  // Lanes holding the same digit are found with one ballot per digit bit (a
+  // 9th bit separates the items past the end, only in the last tile): cheaper
+  // on sm_103a than __match_any_sync.  digit[j] becomes
+  // (rank of the item among the warp's items of its digit) << 9 | digit.
   const uint32_t lt = lanemask_lt();
+  const bool tail_tile = (tile == a.n_tiles - 1);
 #pragma unroll
   for (int j = 0; j < IPT; ++j) {
     const uint32_t d = digit[j];
-    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+    uint32_t peers = 0xFFFFFFFFu;
+#pragma unroll
+    for (int b = 0; b < kRadixBits; ++b) {
+      const uint32_t bit = (d >> b) & 1u;
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, bit);
+      peers &= bit ? m : ~m;
+    }
+    if (tail_tile) {
+      const uint32_t bit = d >> kRadixBits;
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, bit);
+      peers &= bit ? m : ~m;
+    }
     const int leader = __ffs(peers) - 1;
     uint32_t prior = 0;
     if (lane == leader && d < kRadix) {

@@ -151,3 +151,56 @@ def test_tile_shapes_identical(tile_items):
     ref = oracle_of(codes, lens)
     with binding.Context(device=0, tile_items=tile_items) as c:
         assert_same(gpu_bwt(c, codes, lens), ref)
+
+
+PLAN_CASES = ["uniform", "genome", "mixed", "all_a", "identical_cta", "identical_big", "two_letters", "short"]
+
+
+def plan_case(case):
+    rng = np.random.default_rng(17)
+    if case == "uniform":
+        return synth.uniform_reads(20_000, 100, 41)
+    if case == "genome":  # 40x coverage of a 50 kbp genome: groups of ~20 share long prefixes
+        return synth.sample_reads(synth.random_genome(50_000, 42), 20_000, 100, 43, 0.01)
+    if case == "mixed":
+        return synth.mixed_length_reads(10_000, 1, 150, 44)
+    if case == "all_a":  # one huge group whose remainder is finished by the LSD fallback
+        return np.zeros(3000 * 50, dtype=np.uint8), np.full(3000, 50, dtype=np.uint32)
+    if case == "identical_cta":  # groups of 2000 equal suffixes: the CTA sort
+        one = rng.integers(0, 4, size=77).astype(np.uint8)
+        return np.tile(one, 2000), np.full(2000, 77, dtype=np.uint32)
+    if case == "identical_big":  # groups of 3000 equal suffixes: the fallback
+        one = rng.integers(0, 4, size=60).astype(np.uint8)
+        return np.tile(one, 3000), np.full(3000, 60, dtype=np.uint32)
+    if case == "two_letters":
+        lens = rng.integers(20, 60, size=3000).astype(np.uint32)
+        return rng.integers(0, 2, size=int(lens.sum())).astype(np.uint8), lens
+    lens = rng.integers(1, 20, size=5000).astype(np.uint32)  # every suffix within the first window
+    return rng.integers(0, 4, size=int(lens.sum())).astype(np.uint8), lens
+
+
+@pytest.mark.parametrize("case", PLAN_CASES)
+@pytest.mark.parametrize("algorithm", [1, 2])
+def test_plans_identical(case, algorithm):
+    """Both sort plans (LSD over every digit; window-0 LSD + on-chip group
+    finish) give the oracle's result, suffix order included."""
+    from paper_1401_7457_gb300 import binding
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    codes, lens = plan_case(case)
+    ref = oracle_of(codes, lens)
+    with binding.Context(device=0, algorithm=algorithm) as c:
+        assert_same(gpu_bwt(c, codes, lens, want_sa=True), ref, sa=True)
+
+
+def test_group_plan_rejects_long_reads():
+    from paper_1401_7457_gb300 import binding
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    codes, lens = synth.uniform_reads(10, 400, 3)
+    with binding.Context(device=0, algorithm=2) as c:
+        with pytest.raises(binding.CxbwtError) as e:
+            c.build(binding.pack_codes(codes), lens)
+        assert e.value.status == -5
+    with binding.Context(device=0) as c:  # the automatic plan takes the LSD passes instead
+        assert_same(gpu_bwt(c, codes, lens), oracle_of(codes, lens))
