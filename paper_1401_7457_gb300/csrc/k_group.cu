@@ -20,8 +20,9 @@
 //     ones are listed for the host, which finishes them with more LSD passes
 //     restricted to their rows (k_range_hist gives those passes' digit bases).
 //
-// Each warp scans a chunk of rows for group heads, so no group list is
-// materialised for the common case.
+// Each warp walks the groups that start in its chunk of rows in windows of
+// at most 32 rows made of whole groups, and sorts a window with one segmented
+// register network, so no group list is materialised for the common case.
 #include <cuda_runtime.h>
 
 #include "group.cuh"
@@ -69,17 +70,27 @@ __device__ __forceinline__ uint32_t suffix_len(const ReadIndex& R, uint32_t v) {
   return s.len - s.k;
 }
 
-// Sort rows [s, s + m) (m <= 32) of vals by bases 16.. with one warp.
+// Sort the rows of a 32-row window by (group, bases 16.., current position)
+// with one register bitonic network: gid is the first row of the lane's group
+// inside the window (groups are runs of rows, so rows never leave their
+// group), lanes >= n_rows sort last.  Rows of at most 16 bases gather all-zero
+// words, so they keep their place at the front of their group.
 template <int NW>
-__device__ void warp_sort_rows(const SegArgs& a, uint32_t s, uint32_t m, int lane) {
+__device__ void warp_sort_window(const SegArgs& a, uint32_t cur, uint32_t n_rows, uint32_t gid, bool need, int lane) {
   uint32_t w[NW];
   uint32_t v = 0, p = uint32_t(lane);
-  if (uint32_t(lane) < m) {
-    v = a.vals[s + lane];
-    gather_words<NW>(a.R, decode(a.R, v), a.depth, w);
+  uint32_t g = uint32_t(lane) < n_rows ? gid : 32u;
+  if (uint32_t(lane) < n_rows) {
+    v = a.vals[cur + lane];
+    if (need) {
+      gather_words<NW>(a.R, decode(a.R, v), a.depth, w);
+    } else {
+#pragma unroll
+      for (int i = 0; i < NW; ++i) w[i] = 0u;
+    }
   } else {
 #pragma unroll
-    for (int i = 0; i < NW; ++i) w[i] = 0xFFFFFFFFu;  // past the group: sorts last (its position is larger)
+    for (int i = 0; i < NW; ++i) w[i] = 0xFFFFFFFFu;
   }
 #pragma unroll
   for (int k = 2; k <= 32; k <<= 1) {
@@ -90,94 +101,106 @@ __device__ void warp_sort_rows(const SegArgs& a, uint32_t s, uint32_t m, int lan
       for (int i = 0; i < NW; ++i) ow[i] = __shfl_xor_sync(0xFFFFFFFFu, w[i], j);
       const uint32_t ov = __shfl_xor_sync(0xFFFFFFFFu, v, j);
       const uint32_t op = __shfl_xor_sync(0xFFFFFFFFu, p, j);
+      const uint32_t og = __shfl_xor_sync(0xFFFFFFFFu, g, j);
+      const bool other_less = (og != g) ? (og < g) : key_less<NW>(ow, op, w, p);
       const bool ascending = (lane & k) == 0;
       const bool lower = (lane & j) == 0;
-      const bool other_less = key_less<NW>(ow, op, w, p);
-      // The lower lane of an ascending pair keeps the smaller item.
       const bool take = (lower == ascending) ? other_less : !other_less;
       if (take) {
 #pragma unroll
         for (int i = 0; i < NW; ++i) w[i] = ow[i];
         v = ov;
         p = op;
+        g = og;
       }
     }
   }
-  if (uint32_t(lane) < m) a.vals[s + lane] = v;
+  if (uint32_t(lane) < n_rows) a.vals[cur + lane] = v;
 }
 
+// First row r >= from (r < n) whose window differs from row r-1, or n.
+__device__ uint32_t next_head(const SegArgs& a, uint32_t from, int lane) {
+  if (from >= a.n_items) return a.n_items;
+  for (uint32_t x = from;; x += 32) {
+    const uint32_t y = x + lane;
+    const bool head = (y < a.n_items) && (y == 0 || a.keys[y] != a.keys[y - 1]);
+    const bool stop = head || y >= a.n_items;
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, stop);
+    if (m) return min(x + __ffs(m) - 1, a.n_items);
+    if (x - from >= 64) {  // a long run of equal windows: binary search for its end
+      const uint32_t key = a.keys[x + 31];
+      uint32_t lo = x + 32, hi = a.n_items;
+      while (lo < hi) {
+        const uint32_t mid = lo + (hi - lo) / 2;
+        if (a.keys[mid] == key) lo = mid + 1; else hi = mid;
+      }
+      return lo;
+    }
+  }
+}
+
+// Finish one group of more than 32 rows [gs, ge): skip its finished prefix,
+// sort a remainder of at most 32 rows here, list a larger one.
+template <int NW>
+__device__ void finish_long_group(const SegArgs& a, uint32_t gs, uint32_t ge, int lane) {
+  uint32_t lo = gs, hi = ge;
+  while (lo < hi) {
+    const uint32_t mid = lo + (hi - lo) / 2;
+    if (suffix_len(a.R, a.vals[mid]) > a.depth) hi = mid; else lo = mid + 1;
+  }
+  const uint32_t m = ge - lo;
+  if (m < 2) return;
+  if (m <= 32) {
+    warp_sort_window<NW>(a, lo, m, 0u, true, lane);
+  } else if (lane == 0) {
+    const bool cta = m <= kCtaMax;
+    const uint32_t slot = atomicAdd(a.counts + (cta ? 0 : 1), 1u);
+    if (slot < (cta ? a.cta_cap : a.big_cap)) (cta ? a.cta_list : a.big_list)[slot] = make_uint2(lo, m);
+    else atomicOr(a.err, kErrBounds);
+  }
+}
+
+// Each warp owns the groups whose first row lies in its chunk of kChunk rows
+// and walks them in windows of up to 32 rows made of whole groups.
 template <int NW>
 __global__ void __launch_bounds__(256) k_segsort_warp(const SegArgs a) {
   const int lane = threadIdx.x & 31;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t n_chunks = (a.n_items + kChunk - 1) / kChunk;
   for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_chunks; c += warps) {
-    const uint32_t base = c * kChunk;
-    for (uint32_t t = 0; t < kChunk; t += 32) {
-      const uint32_t r = base + t + lane;
-      bool head = false;
-      uint32_t key = 0;
-      if (r < a.n_items) {
-        key = a.keys[r];
-        head = (r == 0) || (a.keys[r - 1] != key);
+    const uint32_t limit = min((c + 1) * kChunk, a.n_items);
+    uint32_t cur = next_head(a, c * kChunk, lane);
+    while (cur < limit) {
+      // Heads among rows cur+1 .. cur+32 (bit l-1 for row cur+l); row limit
+      // and beyond belong to the next chunk's groups, so the first head at or
+      // after limit ends this chunk's last group.
+      const uint32_t y = cur + 1 + lane;
+      bool head = (y >= a.n_items) || (a.keys[y] != a.keys[y - 1]);
+      uint32_t hm = __ballot_sync(0xFFFFFFFFu, head);
+      // Drop heads after the first one at or past limit.
+      const uint32_t past = __ballot_sync(0xFFFFFFFFu, head && y >= limit);
+      if (past) hm &= (past & (~past + 1)) * 2u - 1u;  // keep bits up to the lowest one in past
+      if (hm == 0) {  // the group at cur has more than 32 rows
+        const uint32_t ge = next_head(a, cur + 33, lane);
+        finish_long_group<NW>(a, cur, ge, lane);
+        cur = ge;
+        continue;
       }
-      uint32_t heads = __ballot_sync(0xFFFFFFFFu, head);
-      while (heads) {
-        const int hl = __ffs(heads) - 1;
-        heads &= heads - 1;
-        const uint32_t gs = base + t + hl;
-        const uint32_t gk = __shfl_sync(0xFFFFFFFFu, key, hl);
-        // End of the group: first row after gs whose window differs.
-        uint32_t ge = a.n_items;
-        for (uint32_t x = gs + 1;; x += 32) {
-          const uint32_t y = x + lane;
-          const bool differs = (y >= a.n_items) || (a.keys[y] != gk);
-          const uint32_t m = __ballot_sync(0xFFFFFFFFu, differs);
-          if (m) {
-            ge = x + __ffs(m) - 1;
-            break;
-          }
-          if (x - gs > 64) {  // long group: binary search over the sorted windows
-            uint32_t lo = x + 32, hi = a.n_items;
-            if (lane == 0) {
-              while (lo < hi) {
-                const uint32_t mid = lo + (hi - lo) / 2;
-                if (a.keys[mid] == gk) lo = mid + 1; else hi = mid;
-              }
-            }
-            ge = __shfl_sync(0xFFFFFFFFu, lo, 0);
-            break;
-          }
-        }
-        if (ge - gs < 2) continue;
-        // Skip the finished prefix: members with at most `depth` bases.
-        uint32_t gsr;
-        if (ge - gs <= 32) {
-          const uint32_t y = gs + lane;
-          const bool longer = (y < ge) && suffix_len(a.R, a.vals[y]) > a.depth;
-          const uint32_t m = __ballot_sync(0xFFFFFFFFu, longer);
-          gsr = m ? gs + __ffs(m) - 1 : ge;
-        } else {
-          uint32_t lo = gs, hi = ge;
-          if (lane == 0) {
-            while (lo < hi) {
-              const uint32_t mid = lo + (hi - lo) / 2;
-              if (suffix_len(a.R, a.vals[mid]) > a.depth) hi = mid; else lo = mid + 1;
-            }
-          }
-          gsr = __shfl_sync(0xFFFFFFFFu, lo, 0);
-        }
-        const uint32_t m = ge - gsr;
-        if (m < 2) continue;
-        if (m <= 32) {
-          warp_sort_rows<NW>(a, gsr, m, lane);
-        } else if (lane == 0) {
-          const bool cta = m <= kCtaMax;
-          const uint32_t slot = atomicAdd(a.counts + (cta ? 0 : 1), 1u);
-          if (slot < (cta ? a.cta_cap : a.big_cap)) (cta ? a.cta_list : a.big_list)[slot] = make_uint2(gsr, m);
-          else atomicOr(a.err, kErrBounds);
-        }
+      const uint32_t n_rows = 32u - __clz(hm);  // rows up to the last usable head
+      // Group of row cur+l: the last head at or before it (row cur is a head).
+      const uint32_t heads_at = (hm << 1) | 1u;  // bit l = row cur+l starts a group
+      const uint32_t upto = heads_at & (lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u));
+      const uint32_t gid = 31u - __clz(upto);
+      // A window of only one-row groups is already sorted.
+      const uint32_t full = n_rows == 32 ? 0xFFFFFFFFu : ((1u << n_rows) - 1u);
+      if ((heads_at & full) != full) {
+        // A row that starts a group and is followed by another head (or the
+        // window's end, which is a head) is a group of one: no gather needed.
+        const bool alone = ((heads_at >> lane) & 1u) &&
+                           (lane + 1 >= int(n_rows) || ((heads_at >> (lane + 1)) & 1u));
+        warp_sort_window<NW>(a, cur, n_rows, gid, !alone, lane);
       }
+      cur += n_rows;
     }
   }
 }
