@@ -70,17 +70,19 @@ __device__ __forceinline__ uint32_t suffix_len(const ReadIndex& R, uint32_t v) {
   return s.len - s.k;
 }
 
-// Sort the rows of a 32-row window by (group, bases 16.., current position)
-// with one register bitonic network: gid is the first row of the lane's group
-// inside the window (groups are runs of rows, so rows never leave their
-// group), lanes >= n_rows sort last.  Rows of at most 16 bases gather all-zero
-// words, so they keep their place at the front of their group.
+// Finish the groups of a window of up to 32 rows (lane l holds row cur + l):
+// rows [gid, gend) of the window form the lane's group.  Each row counts the
+// members of its group that order before it - smaller bases 16.. (A-padded),
+// or equal bases and an earlier row (stable) - and moves to gid + that count.
+// Rows of at most 16 bases gather all-zero words, so they keep their place at
+// the front of their group; `need` is false for rows alone in their group.
 template <int NW>
-__device__ void warp_sort_window(const SegArgs& a, uint32_t cur, uint32_t n_rows, uint32_t gid, bool need, int lane) {
+__device__ void warp_rank_window(const SegArgs& a, uint32_t cur, uint32_t n_rows, uint32_t gid, uint32_t gend,
+                                 bool need, int lane) {
+  const bool live = uint32_t(lane) < n_rows;
   uint32_t w[NW];
-  uint32_t v = 0, p = uint32_t(lane);
-  uint32_t g = uint32_t(lane) < n_rows ? gid : 32u;
-  if (uint32_t(lane) < n_rows) {
+  uint32_t v = 0;
+  if (live) {
     v = a.vals[cur + lane];
     if (need) {
       gather_words<NW>(a.R, decode(a.R, v), a.depth, w);
@@ -90,32 +92,28 @@ __device__ void warp_sort_window(const SegArgs& a, uint32_t cur, uint32_t n_rows
     }
   } else {
 #pragma unroll
-    for (int i = 0; i < NW; ++i) w[i] = 0xFFFFFFFFu;
+    for (int i = 0; i < NW; ++i) w[i] = 0u;
   }
+  const uint32_t gsize = live ? gend - gid : 0u;
+  const uint32_t gmax = __reduce_max_sync(0xFFFFFFFFu, gsize);
+  uint32_t rank = 0;
+  for (uint32_t t = 0; t < gmax; ++t) {
+    const uint32_t src = (t < gsize) ? gid + t : uint32_t(lane);
+    uint32_t ow[NW];
 #pragma unroll
-  for (int k = 2; k <= 32; k <<= 1) {
+    for (int i = 0; i < NW; ++i) ow[i] = __shfl_sync(0xFFFFFFFFu, w[i], src);
+    // ow < w, lexicographic, with the row index breaking ties.
+    bool lt = false, eq = true;
 #pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      uint32_t ow[NW];
-#pragma unroll
-      for (int i = 0; i < NW; ++i) ow[i] = __shfl_xor_sync(0xFFFFFFFFu, w[i], j);
-      const uint32_t ov = __shfl_xor_sync(0xFFFFFFFFu, v, j);
-      const uint32_t op = __shfl_xor_sync(0xFFFFFFFFu, p, j);
-      const uint32_t og = __shfl_xor_sync(0xFFFFFFFFu, g, j);
-      const bool other_less = (og != g) ? (og < g) : key_less<NW>(ow, op, w, p);
-      const bool ascending = (lane & k) == 0;
-      const bool lower = (lane & j) == 0;
-      const bool take = (lower == ascending) ? other_less : !other_less;
-      if (take) {
-#pragma unroll
-        for (int i = 0; i < NW; ++i) w[i] = ow[i];
-        v = ov;
-        p = op;
-        g = og;
-      }
+    for (int i = 0; i < NW; ++i) {
+      lt = lt || (eq && ow[i] < w[i]);
+      eq = eq && (ow[i] == w[i]);
     }
+    lt = lt || (eq && src < uint32_t(lane));
+    rank += (src != uint32_t(lane) && lt) ? 1u : 0u;
   }
-  if (uint32_t(lane) < n_rows) a.vals[cur + lane] = v;
+  __syncwarp();  // every lane has read its row before any lane overwrites one
+  if (live && gid + rank != uint32_t(lane)) a.vals[cur + gid + rank] = v;
 }
 
 // First row r >= from (r < n) whose window differs from row r-1, or n.
@@ -151,7 +149,7 @@ __device__ void finish_long_group(const SegArgs& a, uint32_t gs, uint32_t ge, in
   const uint32_t m = ge - lo;
   if (m < 2) return;
   if (m <= 32) {
-    warp_sort_window<NW>(a, lo, m, 0u, true, lane);
+    warp_rank_window<NW>(a, lo, m, 0u, m, true, lane);
   } else if (lane == 0) {
     const bool cta = m <= kCtaMax;
     const uint32_t slot = atomicAdd(a.counts + (cta ? 0 : 1), 1u);
@@ -187,18 +185,17 @@ __global__ void __launch_bounds__(256) k_segsort_warp(const SegArgs a) {
         continue;
       }
       const uint32_t n_rows = 32u - __clz(hm);  // rows up to the last usable head
-      // Group of row cur+l: the last head at or before it (row cur is a head).
-      const uint32_t heads_at = (hm << 1) | 1u;  // bit l = row cur+l starts a group
-      const uint32_t upto = heads_at & (lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u));
-      const uint32_t gid = 31u - __clz(upto);
+      // heads_at bit l: row cur+l starts a group (row cur does).
+      const uint32_t heads_at = (hm << 1) | 1u;
       // A window of only one-row groups is already sorted.
       const uint32_t full = n_rows == 32 ? 0xFFFFFFFFu : ((1u << n_rows) - 1u);
       if ((heads_at & full) != full) {
-        // A row that starts a group and is followed by another head (or the
-        // window's end, which is a head) is a group of one: no gather needed.
-        const bool alone = ((heads_at >> lane) & 1u) &&
-                           (lane + 1 >= int(n_rows) || ((heads_at >> (lane + 1)) & 1u));
-        warp_sort_window<NW>(a, cur, n_rows, gid, !alone, lane);
+        // The lane's group: from the last head at or before it to the next head after it.
+        const uint32_t upto = heads_at & (lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u));
+        const uint32_t gid = 31u - __clz(upto);
+        const uint32_t after = lane == 31 ? 0u : (heads_at & ~((2u << lane) - 1u));
+        const uint32_t gend = after ? min(uint32_t(__ffs(after) - 1), n_rows) : n_rows;
+        warp_rank_window<NW>(a, cur, n_rows, gid, gend, gend - gid > 1, lane);
       }
       cur += n_rows;
     }
