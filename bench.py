@@ -313,6 +313,8 @@ def main():
                 "gpu_launches": int(st["kernel_launches"]), "gpu_launches_per_step": launches_per_step,
                 "clocks": clocks.summary(),
                 "detail": {"step_ms": ms, "sort_pass_ms_per_step": st["sort_pass_ms"] / args.steps,
+                           "group_finish_ms_per_step": st["group_ms"] / args.steps,
+                           "emit_ms_per_step": st["emit_ms"] / args.steps,
                            "build_ms_per_step_lib": st["build_ms"] / args.steps}}
         print(json.dumps(line), flush=True)
     ctx.close()

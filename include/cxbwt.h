@@ -108,7 +108,9 @@ typedef struct {
   uint64_t h2d_bytes;           /* bytes this library copied host -> device */
   uint64_t d2h_bytes;           /* bytes this library copied device -> host */
   uint64_t device_bytes_held;   /* device memory the context holds now */
-  uint64_t reserved[7];
+  double group_ms;              /* device time finishing groups (group plan, only with `timing`) */
+  double emit_ms;               /* device time of the emission (only with `timing`) */
+  uint64_t reserved[5];
 } cxbwt_stats;
 
 /* ABI version of the loaded library (CXBWT_ABI_VERSION it was built with). */

@@ -41,7 +41,8 @@ class Stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_uint64), ("sort_pass_launches", ctypes.c_uint64),
                 ("sort_pass_items", ctypes.c_uint64), ("sort_pass_ms", ctypes.c_double),
                 ("build_ms", ctypes.c_double), ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
-                ("device_bytes_held", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 7)]
+                ("device_bytes_held", ctypes.c_uint64), ("group_ms", ctypes.c_double), ("emit_ms", ctypes.c_double),
+                ("reserved", ctypes.c_uint64 * 5)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

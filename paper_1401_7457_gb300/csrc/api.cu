@@ -53,7 +53,7 @@ struct cxbwt_ctx {
   uint32_t epoch = 0;
   unsigned long long* h_small = nullptr;  // pinned: device error word, length stats
   cudaStream_t last_stream = nullptr;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   cxbwt_stats stats{};
 };
 
@@ -485,6 +485,8 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
     }
   }
 
+  if (timing) CX_CUDA(c, cudaEventRecord(c->ev[4], st));
+
   // ---- 4. emission -----------------------------------------------------------
   const uint64_t bwt_words = (pl.N + 15) / 16;
   uint32_t* d_bwt = out_bwt;
@@ -543,10 +545,14 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   CX_CUDA(c, cudaStreamSynchronize(st));
   CX_TRY(take_device_error(c));
   if (timing) {
-    float ms_sort = 0, ms_all = 0;
+    float ms_sort = 0, ms_all = 0, ms_group = 0, ms_emit = 0;
     CX_CUDA(c, cudaEventElapsedTime(&ms_sort, c->ev[1], c->ev[2]));
+    CX_CUDA(c, cudaEventElapsedTime(&ms_group, c->ev[2], c->ev[4]));
+    CX_CUDA(c, cudaEventElapsedTime(&ms_emit, c->ev[4], c->ev[3]));
     CX_CUDA(c, cudaEventElapsedTime(&ms_all, c->ev[0], c->ev[3]));
     c->stats.sort_pass_ms += ms_sort;
+    c->stats.group_ms += ms_group;
+    c->stats.emit_ms += ms_emit;
     c->stats.build_ms += ms_all;
   }
   c->stats.builds += 1;

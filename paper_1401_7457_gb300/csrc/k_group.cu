@@ -77,42 +77,53 @@ __device__ __forceinline__ uint32_t suffix_len(const ReadIndex& R, uint32_t v) {
 // Rows of at most 16 bases gather all-zero words, so they keep their place at
 // the front of their group; `need` is false for rows alone in their group.
 template <int NW>
+struct RowWords {
+  static constexpr int kStride = (NW + 3) / 4 * 4;  // words per row, a whole number of uint4
+  uint4 r[32][kStride / 4];
+};
+
+template <int NW>
 __device__ void warp_rank_window(const SegArgs& a, uint32_t cur, uint32_t n_rows, uint32_t gid, uint32_t gend,
-                                 bool need, int lane) {
+                                 bool need, int lane, RowWords<NW>& sw) {
+  constexpr int Q = RowWords<NW>::kStride / 4;
   const bool live = uint32_t(lane) < n_rows;
-  uint32_t w[NW];
+  uint32_t w[Q * 4];
   uint32_t v = 0;
+#pragma unroll
+  for (int i = 0; i < Q * 4; ++i) w[i] = 0u;
   if (live) {
     v = a.vals[cur + lane];
     if (need) {
-      gather_words<NW>(a.R, decode(a.R, v), a.depth, w);
-    } else {
+      uint32_t g[NW];
+      gather_words<NW>(a.R, decode(a.R, v), a.depth, g);
 #pragma unroll
-      for (int i = 0; i < NW; ++i) w[i] = 0u;
+      for (int i = 0; i < NW; ++i) w[i] = g[i];
     }
-  } else {
-#pragma unroll
-    for (int i = 0; i < NW; ++i) w[i] = 0u;
   }
-  const uint32_t gsize = live ? gend - gid : 0u;
-  const uint32_t gmax = __reduce_max_sync(0xFFFFFFFFu, gsize);
-  uint32_t rank = 0;
-  for (uint32_t t = 0; t < gmax; ++t) {
-    const uint32_t src = (t < gsize) ? gid + t : uint32_t(lane);
-    uint32_t ow[NW];
+  // Publish this row's words for the other members of its group.
 #pragma unroll
-    for (int i = 0; i < NW; ++i) ow[i] = __shfl_sync(0xFFFFFFFFu, w[i], src);
-    // ow < w, lexicographic, with the row index breaking ties.
+  for (int q = 0; q < Q; ++q) sw.r[lane][q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+  __syncwarp();
+  const uint32_t gsize = live ? gend - gid : 0u;
+  uint32_t rank = 0;
+  for (uint32_t t = 0; t < gsize; ++t) {
+    const uint32_t src = gid + t;
+    // o < w, lexicographic, with the row index breaking ties.
     bool lt = false, eq = true;
 #pragma unroll
-    for (int i = 0; i < NW; ++i) {
-      lt = lt || (eq && ow[i] < w[i]);
-      eq = eq && (ow[i] == w[i]);
+    for (int q = 0; q < Q; ++q) {
+      const uint4 o = sw.r[src][q];  // lanes of one group read one row: a broadcast
+      const uint32_t ov[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        lt = lt || (eq && ov[i] < w[4 * q + i]);
+        eq = eq && (ov[i] == w[4 * q + i]);
+      }
     }
     lt = lt || (eq && src < uint32_t(lane));
-    rank += (src != uint32_t(lane) && lt) ? 1u : 0u;
+    rank += lt ? 1u : 0u;
   }
-  __syncwarp();  // every lane has read its row before any lane overwrites one
+  __syncwarp();  // every lane has read its row and the shared words before any overwrite
   if (live && gid + rank != uint32_t(lane)) a.vals[cur + gid + rank] = v;
 }
 
@@ -140,7 +151,7 @@ __device__ uint32_t next_head(const SegArgs& a, uint32_t from, int lane) {
 // Finish one group of more than 32 rows [gs, ge): skip its finished prefix,
 // sort a remainder of at most 32 rows here, list a larger one.
 template <int NW>
-__device__ void finish_long_group(const SegArgs& a, uint32_t gs, uint32_t ge, int lane) {
+__device__ void finish_long_group(const SegArgs& a, uint32_t gs, uint32_t ge, int lane, RowWords<NW>& sw) {
   uint32_t lo = gs, hi = ge;
   while (lo < hi) {
     const uint32_t mid = lo + (hi - lo) / 2;
@@ -149,7 +160,7 @@ __device__ void finish_long_group(const SegArgs& a, uint32_t gs, uint32_t ge, in
   const uint32_t m = ge - lo;
   if (m < 2) return;
   if (m <= 32) {
-    warp_rank_window<NW>(a, lo, m, 0u, m, true, lane);
+    warp_rank_window<NW>(a, lo, m, 0u, m, true, lane, sw);
   } else if (lane == 0) {
     const bool cta = m <= kCtaMax;
     const uint32_t slot = atomicAdd(a.counts + (cta ? 0 : 1), 1u);
@@ -163,6 +174,8 @@ __device__ void finish_long_group(const SegArgs& a, uint32_t gs, uint32_t ge, in
 template <int NW>
 __global__ void __launch_bounds__(256) k_segsort_warp(const SegArgs a) {
   const int lane = threadIdx.x & 31;
+  __shared__ RowWords<NW> s_rows[8];
+  RowWords<NW>& sw = s_rows[threadIdx.x >> 5];
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t n_chunks = (a.n_items + kChunk - 1) / kChunk;
   for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_chunks; c += warps) {
@@ -180,7 +193,7 @@ __global__ void __launch_bounds__(256) k_segsort_warp(const SegArgs a) {
       if (past) hm &= (past & (~past + 1)) * 2u - 1u;  // keep bits up to the lowest one in past
       if (hm == 0) {  // the group at cur has more than 32 rows
         const uint32_t ge = next_head(a, cur + 33, lane);
-        finish_long_group<NW>(a, cur, ge, lane);
+        finish_long_group<NW>(a, cur, ge, lane, sw);
         cur = ge;
         continue;
       }
@@ -195,7 +208,7 @@ __global__ void __launch_bounds__(256) k_segsort_warp(const SegArgs a) {
         const uint32_t gid = 31u - __clz(upto);
         const uint32_t after = lane == 31 ? 0u : (heads_at & ~((2u << lane) - 1u));
         const uint32_t gend = after ? min(uint32_t(__ffs(after) - 1), n_rows) : n_rows;
-        warp_rank_window<NW>(a, cur, n_rows, gid, gend, gend - gid > 1, lane);
+        warp_rank_window<NW>(a, cur, n_rows, gid, gend, gend - gid > 1, lane, sw);
       }
       cur += n_rows;
     }
