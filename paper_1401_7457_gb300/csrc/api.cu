@@ -338,7 +338,8 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   const bool timing = c->opt.timing != 0;
   if (timing) CX_CUDA(c, cudaEventRecord(c->ev[0], st));
 
-  ReadIndex R{d_reads, pl.n_words, d_desc, pl.shift, pl.uniform ? pl.Lmax : 0u, uint32_t(n)};
+  ReadIndex R{d_reads, pl.n_words, d_desc, pl.shift, pl.uniform ? pl.Lmax : 0u, uint32_t(n),
+              (reinterpret_cast<uintptr_t>(d_reads) & 15u) == 0 ? 1u : 0u};
 
   // ---- 1. all-digit histogram -----------------------------------------------
   CX_CUDA(c, launch_poscount(R, uint32_t(n), pl.Lmax, static_cast<uint32_t*>(c->P.p), c->sm_count, st));

@@ -35,6 +35,7 @@ struct ReadIndex {
   uint32_t shift;         // v = (read << shift) | offset
   uint32_t uniform_len;   // L when desc == nullptr
   uint32_t n_reads;
+  uint32_t words_aligned; // nonzero when `words` is 16-byte aligned (vector loads allowed)
 };
 
 struct Suffix {
@@ -75,8 +76,17 @@ __device__ __forceinline__ uint32_t window16(const ReadIndex& R, const Suffix& s
   const uint64_t q = s.off + rel;
   const uint64_t w = q >> 4;
   const uint32_t sh = uint32_t(q & 15u) * 2u;
-  const uint32_t first = load_word(R, w);
-  const uint32_t next = sh ? load_word(R, w + 1) : 0u;
+  uint32_t first, next;
+  const uint32_t o = uint32_t(w & 3u);
+  if (R.words_aligned && o < 3 && w + 1 < R.n_words) {
+    // Both words sit in one aligned 16-byte chunk: one load.
+    const uint4 c = __ldg(reinterpret_cast<const uint4*>(R.words) + (w >> 2));
+    first = o == 0 ? c.x : o == 1 ? c.y : c.z;
+    next = o == 0 ? c.y : o == 1 ? c.z : c.w;
+  } else {
+    first = load_word(R, w);
+    next = sh ? load_word(R, w + 1) : 0u;
+  }
   // top 32 bits of (first:next) << sh
   uint32_t key = __funnelshift_l(next, first, sh);
   if (rem < 16u) key &= ~(0xFFFFFFFFu >> (2u * rem));

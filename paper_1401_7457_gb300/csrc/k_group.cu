@@ -32,27 +32,54 @@ namespace {
 
 constexpr int kChunk = 256;  // rows scanned per warp task
 
+// Word x of the store read as part of aligned 4-word chunks: chunk c holds
+// words 4c .. 4c+3 and is fetched with one 16-byte load when it lies wholly
+// inside the store (the store base is 16-byte aligned: checked by the host).
+__device__ __forceinline__ uint4 load_chunk(const ReadIndex& R, uint64_t c) {
+  if (4 * c + 3 < R.n_words) return __ldg(reinterpret_cast<const uint4*>(R.words) + c);
+  return make_uint4(load_word(R, 4 * c), load_word(R, 4 * c + 1), load_word(R, 4 * c + 2), load_word(R, 4 * c + 3));
+}
+
 // Bases [c0, c0 + 16*NW) of suffix s (A-padded past the read end) as NW words.
+// The NW + 1 store words it spans are fetched as at most NW/4 + 2 aligned
+// 16-byte chunks (one L1 request each) instead of word by word.
 template <int NW>
 __device__ __forceinline__ void gather_words(const ReadIndex& R, const Suffix& s, uint32_t c0, uint32_t (&w)[NW]) {
   const uint32_t rel = s.k + c0;
   const uint32_t rem = rel < s.len ? s.len - rel : 0u;  // real bases from c0 on
+#pragma unroll
+  for (int i = 0; i < NW; ++i) w[i] = 0u;
+  if (rem == 0) return;
   const uint64_t q = s.off + rel;
   const uint64_t w0 = q >> 4;
   const uint32_t sh = uint32_t(q & 15u) * 2u;
-  uint32_t prev = rem ? load_word(R, w0) : 0u;
+  const uint32_t o = uint32_t(w0 & 3u);  // offset of w0 in its chunk
+  constexpr int CH = NW / 4 + 2;         // chunks covering words w0 .. w0 + NW
+  uint32_t b[4 * CH];
+  const uint32_t words_needed = min(uint32_t(NW), (rem + 15u) / 16u) + 1u;
+  const uint32_t chunks = (o + words_needed + 3u) / 4u;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    uint4 x = make_uint4(0u, 0u, 0u, 0u);
+    if (uint32_t(c) < chunks) x = R.words_aligned ? load_chunk(R, (w0 >> 2) + c)
+                                                  : make_uint4(load_word(R, w0 - o + 4 * c), load_word(R, w0 - o + 4 * c + 1),
+                                                               load_word(R, w0 - o + 4 * c + 2),
+                                                               load_word(R, w0 - o + 4 * c + 3));
+    b[4 * c] = x.x; b[4 * c + 1] = x.y; b[4 * c + 2] = x.z; b[4 * c + 3] = x.w;
+  }
+  // Word i of the suffix window is store word w0 + i = b[o + i]; pick it
+  // without dynamic register indexing.
 #pragma unroll
   for (int i = 0; i < NW; ++i) {
-    const uint32_t need = 16u * i;  // bases of the read before word i
-    uint32_t x = 0;
+    const uint32_t need = 16u * i;
     if (need < rem) {
-      const uint32_t next = load_word(R, w0 + i + 1);
-      x = __funnelshift_l(next, prev, sh);
-      prev = next;
+      const uint32_t lo = o == 0 ? b[i] : o == 1 ? b[i + 1] : o == 2 ? b[i + 2] : b[i + 3];
+      const uint32_t hi = o == 0 ? b[i + 1] : o == 1 ? b[i + 2] : o == 2 ? b[i + 3] : b[i + 4];
+      uint32_t x = __funnelshift_l(hi, lo, sh);
       const uint32_t left = rem - need;
       if (left < 16u) x &= ~(0xFFFFFFFFu >> (2u * left));
+      w[i] = x;
     }
-    w[i] = x;
   }
 }
 
