@@ -81,8 +81,17 @@ typedef struct {
   int async;                    /* nonzero: calls return after enqueue when outputs are on the device */
   int timing;                   /* nonzero: record CUDA events around every phase (see cxbwt_stats) */
   int algorithm;                /* CXBWT_ALGO_*: how the suffixes are sorted (all give identical output) */
-  int reserved[7];
+  int plan_flags;               /* CXBWT_PLAN_* bits: force plan choices normally made by size (testing, tuning) */
+  int reserved[6];
 } cxbwt_options;
+
+/* plan_flags bits.  None changes the result.
+ *  ID64        - carry 64-bit suffix ids even when 32 bits would do.
+ *  READ_MAJOR  - when the build needs several slices, enumerate suffixes in
+ *                read-major order (store read in address order) even when the
+ *                store would fit L2. */
+#define CXBWT_PLAN_ID64 1
+#define CXBWT_PLAN_READ_MAJOR 2
 
 /* Sort plans.  Every plan computes the same B_R; they differ in speed only.
  *  AUTO     - GROUPS when the reads are at most 272 bases, else LSD.
@@ -110,7 +119,8 @@ typedef struct {
   uint64_t device_bytes_held;   /* device memory the context holds now */
   double group_ms;              /* device time finishing groups (group plan, only with `timing`) */
   double emit_ms;               /* device time of the emission (only with `timing`) */
-  uint64_t reserved[5];
+  uint64_t slices;              /* device-memory-bounded slices sorted (one per build when it fits) */
+  uint64_t reserved[4];
 } cxbwt_stats;
 
 /* ABI version of the loaded library (CXBWT_ABI_VERSION it was built with). */

@@ -33,7 +33,8 @@ class CxbwtError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("device_budget_bytes", ctypes.c_uint64), ("device", ctypes.c_int), ("prefix_len", ctypes.c_int),
                 ("digit_bits", ctypes.c_int), ("tile_items", ctypes.c_int), ("async_", ctypes.c_int),
-                ("timing", ctypes.c_int), ("algorithm", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("timing", ctypes.c_int), ("algorithm", ctypes.c_int), ("plan_flags", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 class Stats(ctypes.Structure):
@@ -42,7 +43,7 @@ class Stats(ctypes.Structure):
                 ("sort_pass_items", ctypes.c_uint64), ("sort_pass_ms", ctypes.c_double),
                 ("build_ms", ctypes.c_double), ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
                 ("device_bytes_held", ctypes.c_uint64), ("group_ms", ctypes.c_double), ("emit_ms", ctypes.c_double),
-                ("reserved", ctypes.c_uint64 * 5)]
+                ("slices", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 4)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -168,9 +169,10 @@ class Context:
     """One cxbwt context (device workspace + bookkeeping) on one device."""
 
     ALGO_AUTO, ALGO_LSD, ALGO_GROUPS = 0, 1, 2
+    PLAN_ID64, PLAN_READ_MAJOR = 1, 2
 
     def __init__(self, device: int = 0, budget_bytes: int = 0, async_: bool = False, timing: bool = False,
-                 tile_items: int = 0, algorithm: int = 0):
+                 tile_items: int = 0, algorithm: int = 0, plan_flags: int = 0):
         L = lib()
         opt = Options()
         L.cxbwt_default_options(ctypes.byref(opt))
@@ -180,6 +182,7 @@ class Context:
         opt.timing = 1 if timing else 0
         opt.tile_items = tile_items
         opt.algorithm = algorithm
+        opt.plan_flags = plan_flags
         h = ctypes.c_void_p()
         st = L.cxbwt_create(ctypes.byref(h), ctypes.byref(opt))
         if st != 0:

@@ -1,17 +1,27 @@
-// The C ABI of include/cxbwt.h: validation, device workspace, the pass plan
-// of the LSD suffix sort, launches, and the host helpers.
+// The C ABI of include/cxbwt.h: validation, device workspace, the plan of a
+// build, launches, and the host helpers.
 //
-// A build runs, on the caller's stream:
-//   1. the all-digit histogram (k_poscount + k_digitbase): Figure 2 step 1's
-//      scan of all suffixes, turned into the first output row of every digit
+// A build sorts one or more "slices" of the suffixes and emits each slice's
+// part of the BWT at its global row offset.  A slice is the whole collection
+// when its workspace fits the device budget; otherwise the planner of Figure
+// 2 steps 1-3 applies: one scan counts the suffixes of every bucket (first 8
+// bases), consecutive buckets are packed into slices of at most m1 suffixes
+// (m1 from the budget), and each slice rescans all suffixes keeping those of
+// its buckets (the listing of step 3(a)).  Per slice, on the caller's stream:
+//   1. digit histograms: k_poscount + k_digitbase (whole collection) or
+//      k_pass_hist (the slice's buckets) - the first output row of every digit
 //      value of every pass;
-//   2. for reads of different lengths, the (suffix length, read) start order
-//      (k_identity + one or two length passes); for one common length that
-//      order is generated inside the first digit pass;
+//   2. the (suffix length, read) start order: generated inside the first
+//      digit pass for reads of one length (in read-major order plus a
+//      suffix-length digit when the store is too big for L2), or k_identity
+//      plus length passes for mixed lengths;
 //   3. the LSD digit passes (Section 3.2), least significant 4-base digit
 //      first, each 16-base stringword window gathered once and carried in the
-//      key array for its remaining passes;
-//   4. emission (Figure 2 step 3(c)(iii)).
+//      key array for its remaining passes - every window (LSD plan) or only
+//      the first (group plan, followed by the on-chip group finish);
+//   4. emission (Figure 2 step 3(c)(iii)); with host outputs, the finished
+//      words of each slice stream to the host on a side stream while the
+//      next slice sorts.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,8 +59,11 @@ struct cxbwt_ctx {
   uint64_t held = 0;
   std::string err;
 
-  DevBuf vals[2], keys[2], status, P, base, lenhist, desc, misc, store, out_bwt, out_dollar, out_sa, seglist, rhist;
+  DevBuf vals[2], keys[2], status, P, base, lenhist, desc, misc, store, out_bwt, out_dollar, out_sa, seglist, rhist,
+      bhist;
   uint32_t epoch = 0;
+  cudaStream_t side = nullptr;            // device -> host streaming of finished slices
+  cudaEvent_t slice_done[2] = {nullptr, nullptr};
   unsigned long long* h_small = nullptr;  // pinned: device error word, length stats
   cudaStream_t last_stream = nullptr;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -87,7 +100,9 @@ int fail(cxbwt_ctx* c, int status, const char* fmt, ...) {
 // Grow-only device buffer within the context's budget.
 int ensure(cxbwt_ctx* c, DevBuf& b, size_t bytes, const char* what) {
   if (b.cap >= bytes) return CXBWT_OK;
-  const size_t want = std::max<size_t>((bytes + (1u << 21) - 1) & ~size_t((1u << 21) - 1), 1u << 21);
+  // Large buffers grow in 2 MB steps (fewer regrows), small ones in 64 KB steps.
+  const size_t step = bytes >= (size_t(64) << 20) ? (size_t(1) << 21) : (size_t(1) << 16);
+  const size_t want = std::max<size_t>((bytes + step - 1) & ~(step - 1), step);
   if (c->held - b.cap + want > c->budget)
     return fail(c, CXBWT_ENOMEM, "device budget of %llu bytes exceeded growing %s to %zu bytes",
                 (unsigned long long)c->budget, what, want);
@@ -140,6 +155,8 @@ uint32_t bits_for(uint32_t x) {  // smallest s with 2^s > x
   return s;
 }
 
+constexpr uint32_t kBucketBits = 16;  // slices are ranges of buckets of the first 8 bases
+
 struct Plan {
   uint64_t n = 0, sum = 0, N = 0;
   uint32_t Lmin = 0, Lmax = 0, shift = 0;
@@ -148,6 +165,37 @@ struct Plan {
   uint32_t W = 0;         // 16-base windows
   uint32_t len_passes = 0;
   uint64_t n_words = 0;
+  int idb = 4;            // suffix id bytes
+  bool groups = false;
+  int seg_words = 0;
+  uint32_t w_last = 0;    // windows [0, w_last] are sorted by LSD passes over all rows of a slice
+};
+
+struct Slice {
+  bool whole = true;          // every suffix (no bucket filter)
+  uint32_t lo = 0, hi = 0;    // bucket range when not whole
+  uint32_t rows = 0;          // suffixes in the slice
+  uint64_t row0 = 0;          // global BWT row of its first suffix
+};
+
+// Per-build device state shared by the slices.
+struct Run {
+  cudaStream_t st = nullptr;
+  Plan pl;
+  ReadIndex R{};
+  TileShape shape{};
+  void* vals[2] = {nullptr, nullptr};
+  uint32_t* keys[2] = {nullptr, nullptr};
+  uint32_t* base = nullptr;
+  uint32_t* d_err = nullptr;
+  uint32_t* d_counter = nullptr;
+  uint32_t* d_seg = nullptr;
+  unsigned long long* d_counts = nullptr;
+  uint32_t* d_bwt = nullptr;      // global word w at d_bwt[w]
+  uint64_t* d_dollar = nullptr;
+  uint64_t* d_sa = nullptr;       // global rows
+  bool read_major = false;        // multi-slice first pass in read-major order
+  uint64_t launches = 0, sort_launches = 0, sort_items = 0, d2h = 0;
 };
 
 // Reads the device error word (already copied to h_small[4] by a completed
@@ -163,6 +211,194 @@ int take_device_error(cxbwt_ctx* c) {
   if (derr & kErrBounds)
     return fail(c, CXBWT_EINTERNAL, "a sort pass or the emission met an out-of-range row or suffix id");
   return fail(c, CXBWT_EINTERNAL, "device check failed (error word 0x%x)", derr);
+}
+
+void* vptr(void* base, int idb, uint64_t row) { return static_cast<char*>(base) + row * uint64_t(idb); }
+
+// Sort the slice's suffixes into r.vals[cur]; returns cur (0 or 1) through *cur_out.
+int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out) {
+  const Plan& pl = r.pl;
+  cudaStream_t st = r.st;
+  const uint32_t TILE = uint32_t(r.shape.tile());
+  PassArgs a{};
+  a.status = static_cast<unsigned long long*>(c->status.p);
+  a.tile_counter = r.d_counter;
+  a.err = r.d_err;
+  a.R = r.R;
+  a.n_reads = uint32_t(pl.n);
+  a.timeout_ns = kTimeoutNs;
+  a.bucket_shift = 32 - kBucketBits;
+  a.bucket_lo = sl.lo;
+  a.bucket_hi = sl.hi;
+  const uint32_t d_sorted = std::min<uint32_t>(pl.D, 4 * (pl.w_last + 1));
+
+  // ---- digit bases -----------------------------------------------------------
+  // whole: rows 0..d_sorted-1 = char digits d, rows D.. = length digits.
+  // slice: rows 0 = suffix length, 1..4 = window-0 digits (most significant first).
+  if (sl.whole) {
+    CX_CUDA(c, cudaMemsetAsync(c->P.p, 0, uint64_t(pl.Lmax) * kRadix * 4, st));
+    CX_CUDA(c, launch_poscount(r.R, uint32_t(pl.n), pl.Lmax, static_cast<uint32_t*>(c->P.p), c->sm_count, st));
+    CX_CUDA(c, launch_digitbase(static_cast<const uint32_t*>(c->P.p), pl.Lmax, d_sorted, pl.uniform ? 1 : 0,
+                                uint32_t(pl.n), pl.Lmax, static_cast<const uint32_t*>(c->lenhist.p), r.base, st));
+    r.launches += 2;
+  } else {
+    CX_CUDA(c, cudaMemsetAsync(r.base, 0, 5 * kRadix * 4, st));
+    CX_CUDA(c, launch_pass_hist(r.R, uint32_t(pl.n), kBucketBits, sl.lo, sl.hi, r.base, c->sm_count, st));
+    r.launches += 2;
+  }
+  auto digit_base = [&](uint32_t d) -> const uint32_t* {  // char digit d of window 0 (or any window when whole)
+    if (sl.whole) return r.base + size_t(d) * kRadix;
+    return r.base + size_t(1 + d) * kRadix;  // d in 0..3
+  };
+
+  int cur = 0, kin = 0;
+  const int idb = pl.idb;
+  bool first = pl.uniform;  // the first digit pass generates the start order
+  a.n_gen = sl.whole ? pl.N : pl.N;  // generated passes enumerate every suffix
+  a.n_out = sl.rows;
+  a.n_tiles = uint32_t((pl.N + TILE - 1) / TILE);
+  if (!pl.uniform) {
+    // Mixed lengths (whole collection only): id list in read order, then
+    // stable passes over the suffix length.
+    CX_CUDA(c, launch_identity(r.R, uint32_t(pl.n), r.vals[0], idb, st));
+    ++r.launches;
+    a.n_gen = sl.rows;
+    a.n_tiles = uint32_t((uint64_t(sl.rows) + TILE - 1) / TILE);
+    for (uint32_t j = 0; j < pl.len_passes; ++j) {
+      a.vals_in = r.vals[cur];
+      a.vals_out = r.vals[cur ^ 1];
+      a.keys_in = nullptr;
+      a.keys_out = nullptr;
+      a.digit_base = r.base + size_t(pl.D + j) * kRadix;
+      a.key_shift = 8 * j;
+      a.window_c0 = 0;
+      a.epoch = ++c->epoch;
+      CX_CUDA(c, launch_onesweep(a, kSrcLength, false, false, idb, r.shape, st));
+      cur ^= 1;
+      ++r.sort_launches;
+      r.sort_items += sl.rows;
+    }
+  } else if (r.read_major) {
+    // Read-major generated order (the store is read in address order),
+    // filtered to the slice, stably sorted by suffix length, window 0 carried.
+    a.vals_in = nullptr;
+    a.vals_out = r.vals[cur ^ 1];
+    a.keys_in = nullptr;
+    a.keys_out = r.keys[kin];
+    a.digit_base = r.base;  // row 0: suffix length
+    a.key_shift = 0;
+    a.window_c0 = 0;
+    a.epoch = ++c->epoch;
+    CX_CUDA(c, launch_onesweep(a, kSrcInitReadMajor, true, !sl.whole, idb, r.shape, st));
+    cur ^= 1;
+    ++r.sort_launches;
+    r.sort_items += sl.rows;
+    first = false;
+  }
+  for (int64_t w = int64_t(pl.w_last); w >= 0; --w) {
+    const uint32_t d_lo = uint32_t(4 * w);
+    const uint32_t d_hi = std::min<uint32_t>(d_lo + 3, pl.D - 1);
+    for (int64_t d = d_hi; d >= int64_t(d_lo); --d) {
+      const bool first_in_window = (uint32_t(d) == d_hi);
+      const bool last_in_window = (uint32_t(d) == d_lo);
+      const bool carried = !first_in_window || (w == 0 && r.read_major && pl.uniform);
+      const int mode = carried ? kSrcCarried : (first ? kSrcInitUniform : kSrcExtract);
+      // The group plan keeps the window-0 keys of the final order: groups are runs of equal keys.
+      const bool write_key = !last_in_window || pl.groups;
+      const bool generated = (mode == kSrcInitUniform);
+      a.n_gen = generated ? pl.N : sl.rows;
+      a.n_tiles = uint32_t((a.n_gen + TILE - 1) / TILE);
+      a.vals_in = generated ? nullptr : r.vals[cur];
+      a.vals_out = r.vals[cur ^ 1];
+      a.keys_in = (mode == kSrcCarried) ? r.keys[kin] : nullptr;
+      const int kout = (mode == kSrcCarried) ? (kin ^ 1) : kin;
+      a.keys_out = write_key ? r.keys[kout] : nullptr;
+      a.digit_base = digit_base(uint32_t(d));
+      a.key_shift = 24u - 8u * uint32_t(d - d_lo);
+      a.window_c0 = uint32_t(16 * w);
+      a.epoch = ++c->epoch;
+      CX_CUDA(c, launch_onesweep(a, mode, write_key, generated && !sl.whole, idb, r.shape, st));
+      cur ^= 1;
+      if (write_key) kin = kout;
+      first = false;
+      ++r.sort_launches;
+      r.sort_items += sl.rows;
+    }
+  }
+  if (c->opt.timing && sl.row0 == 0) CX_CUDA(c, cudaEventRecord(c->ev[2], st));
+
+  // ---- group plan: finish every group of equal first windows on chip ---------
+  if (pl.groups && pl.Lmax > 16) {
+    const uint64_t cta_cap = uint64_t(sl.rows) / 33 + 1, big_cap = uint64_t(sl.rows) / kCtaMax + 1;
+    CX_CUDA(c, cudaMemsetAsync(r.d_seg, 0, 16, st));
+    SegArgs g{};
+    g.keys = r.keys[kin];
+    g.vals = r.vals[cur];
+    g.n_items = sl.rows;
+    g.R = r.R;
+    g.depth = 16;
+    g.cta_list = static_cast<uint2*>(c->seglist.p);
+    g.cta_cap = uint32_t(cta_cap);
+    g.big_list = g.cta_list + cta_cap;
+    g.big_cap = uint32_t(big_cap);
+    g.counts = r.d_seg;
+    g.err = r.d_err;
+    CX_CUDA(c, launch_segsort(g, pl.seg_words, idb, c->sm_count, st));
+    r.launches += 2;
+    // Remainders too large for one CTA (rare: long runs of equal bases) are
+    // finished here with LSD passes over bases 16.. restricted to their rows.
+    CX_CUDA(c, cudaMemcpyAsync(c->h_small + 5, r.d_seg, 8, cudaMemcpyDeviceToHost, st));
+    CX_CUDA(c, cudaStreamSynchronize(st));
+    const uint32_t n_big = std::min<uint32_t>(reinterpret_cast<const uint32_t*>(c->h_small + 5)[1], g.big_cap);
+    if (n_big) {
+      std::vector<uint2> big(n_big);
+      CX_CUDA(c, cudaMemcpyAsync(big.data(), g.big_list, n_big * 8, cudaMemcpyDeviceToHost, st));
+      CX_CUDA(c, cudaStreamSynchronize(st));
+      r.d2h += n_big * 8;
+      const uint32_t n_win = pl.W - 1;
+      auto* rh = static_cast<uint32_t*>(c->rhist.p);
+      for (const uint2& bg : big) {
+        const uint32_t s0 = bg.x, m = bg.y;
+        CX_CUDA(c, cudaMemsetAsync(rh, 0, size_t(n_win) * 4 * kRadix * 4, st));
+        CX_CUDA(c, launch_range_hist(vptr(r.vals[cur], idb, s0), idb, m, r.R, n_win, rh, c->sm_count, st));
+        r.launches += 2;
+        void* gv[2] = {vptr(r.vals[cur], idb, s0), vptr(r.vals[cur ^ 1], idb, s0)};
+        uint32_t* gk[2] = {r.keys[0] + s0, r.keys[1] + s0};
+        int gc = 0, gki = 0;
+        PassArgs b = a;
+        b.n_gen = m;
+        b.n_out = m;
+        b.n_tiles = uint32_t((m + TILE - 1) / TILE);
+        for (uint32_t w = pl.W - 1; w >= 1; --w) {
+          const uint32_t d_lo = 4 * w;
+          const uint32_t d_hi = std::min<uint32_t>(d_lo + 3, pl.D - 1);
+          for (int64_t d = d_hi; d >= int64_t(d_lo); --d) {
+            const bool first_in_window = (uint32_t(d) == d_hi);
+            const bool last_in_window = (uint32_t(d) == d_lo);
+            const int mode = first_in_window ? kSrcExtract : kSrcCarried;
+            const bool write_key = !last_in_window;
+            b.vals_in = gv[gc];
+            b.vals_out = gv[gc ^ 1];
+            b.keys_in = (mode == kSrcCarried) ? gk[gki] : nullptr;
+            const int kout = (mode == kSrcCarried) ? (gki ^ 1) : gki;
+            b.keys_out = write_key ? gk[kout] : nullptr;
+            b.digit_base = rh + size_t((w - 1) * 4 + (uint32_t(d) - d_lo)) * kRadix;
+            b.key_shift = 24u - 8u * (uint32_t(d) - d_lo);
+            b.window_c0 = 16 * w;
+            b.epoch = ++c->epoch;
+            CX_CUDA(c, launch_onesweep(b, mode, write_key, false, idb, r.shape, st));
+            gc ^= 1;
+            if (write_key) gki = kout;
+            ++r.sort_launches;
+            r.sort_items += m;
+          }
+        }
+        if (gc) CX_CUDA(c, cudaMemcpyAsync(gv[0], gv[1], size_t(m) * idb, cudaMemcpyDeviceToDevice, st));
+      }
+    }
+  }
+  *cur_out = cur;
+  return CXBWT_OK;
 }
 
 int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* lens, uint32_t* out_bwt,
@@ -181,23 +417,23 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   const bool dollar_dev = out_dollar && is_device_ptr(out_dollar);
   const bool counts_dev = out_counts && is_device_ptr(out_counts);
   const bool sa_dev = out_sa && is_device_ptr(out_sa);
-  uint64_t launches = 0, h2d = 0, d2h = 0;
+  Run r;
+  r.st = st;
+  uint64_t h2d = 0;
 
   CX_TRY(ensure(c, c->misc, kMiscBytes, "scratch words"));
   char* misc = static_cast<char*>(c->misc.p);
-  auto* d_err = reinterpret_cast<uint32_t*>(misc + kMiscErr);
-  auto* d_counter = reinterpret_cast<uint32_t*>(misc + kMiscTileCounter);
-  auto* d_counts = reinterpret_cast<unsigned long long*>(misc + kMiscCounts);
+  r.d_err = reinterpret_cast<uint32_t*>(misc + kMiscErr);
+  r.d_counter = reinterpret_cast<uint32_t*>(misc + kMiscTileCounter);
+  r.d_counts = reinterpret_cast<unsigned long long*>(misc + kMiscCounts);
+  r.d_seg = reinterpret_cast<uint32_t*>(misc + kMiscSeg);
   auto* d_lstats = reinterpret_cast<unsigned long long*>(misc + kMiscLenStats);
 
   // ---- read lengths ------------------------------------------------------
-  Plan pl;
+  Plan& pl = r.pl;
   pl.n = n;
   std::vector<uint32_t> lens_copy;
-  const uint32_t* hlens = nullptr;
-  if (!lens_dev) {
-    hlens = lens;
-  }
+  const uint32_t* hlens = lens_dev ? nullptr : lens;
   uint64_t mn = ~0ull, mx = 0, sum = 0, bad = 0;
   if (hlens) {
     for (uint64_t i = 0; i < n; ++i) {
@@ -211,10 +447,10 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
     const unsigned long long init[4] = {~0ull, 0, 0, 0};
     CX_CUDA(c, cudaMemcpyAsync(d_lstats, init, sizeof init, cudaMemcpyHostToDevice, st));
     CX_CUDA(c, launch_lenstats(lens, n, d_lstats, st));
-    ++launches;
+    ++r.launches;
     CX_CUDA(c, cudaMemcpyAsync(c->h_small, d_lstats, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CX_CUDA(c, cudaStreamSynchronize(st));
-    d2h += 32;
+    r.d2h += 32;
     mn = c->h_small[0];
     mx = c->h_small[1];
     sum = c->h_small[2];
@@ -231,25 +467,24 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   pl.W = (pl.Lmax + 15) / 16;
   pl.len_passes = pl.uniform ? 0 : (pl.Lmax > 255 ? 2 : 1);
   pl.n_words = (sum + 15) / 16;
-  const int seg_words = segsort_words(pl.Lmax);
-  bool groups;
+  pl.seg_words = segsort_words(pl.Lmax);
   switch (c->opt.algorithm) {
-    case CXBWT_ALGO_LSD: groups = false; break;
+    case CXBWT_ALGO_LSD: pl.groups = false; break;
     case CXBWT_ALGO_GROUPS:
-      if (!seg_words) return fail(c, CXBWT_EUNSUPPORTED, "the group plan handles reads of at most 272 bases");
-      groups = true;
+      if (!pl.seg_words) return fail(c, CXBWT_EUNSUPPORTED, "the group plan handles reads of at most 272 bases");
+      pl.groups = true;
       break;
-    case CXBWT_ALGO_AUTO: groups = seg_words != 0; break;
+    case CXBWT_ALGO_AUTO: pl.groups = pl.seg_words != 0; break;
     default: return fail(c, CXBWT_EINVAL, "unknown algorithm %d", c->opt.algorithm);
   }
   // Windows [0, w_last] are sorted by LSD passes over all rows; with the
   // group plan only window 0 is, and the groups are finished on chip.
-  const uint32_t w_last = groups ? 0u : pl.W - 1;
-  const uint32_t d_sorted = std::min<uint32_t>(pl.D, 4 * (w_last + 1));
-  const uint64_t max_value = ((n - 1) << pl.shift) | pl.Lmax;
-  if (pl.shift > 31 || ((n - 1) >> (32 - pl.shift)) != 0 || max_value > 0xFFFFFFFFull)
-    return fail(c, CXBWT_EUNSUPPORTED, "n_reads x 2^%u exceeds the 32-bit suffix id space of one sort", pl.shift);
-  if (pl.N >= (uint64_t(1) << 32)) return fail(c, CXBWT_EUNSUPPORTED, "more than 2^32 - 1 suffixes in one sort");
+  pl.w_last = pl.groups ? 0u : pl.W - 1;
+  const uint64_t max_id = ((n - 1) << pl.shift) | pl.Lmax;
+  pl.idb = (pl.shift <= 31 && ((n - 1) >> (32 - pl.shift)) == 0 && max_id <= 0xFFFFFFFFull) ? 4 : 8;
+  if (c->opt.plan_flags & CXBWT_PLAN_ID64) pl.idb = 8;
+  r.shape = onesweep_shape(c->opt.tile_items, pl.idb);
+  const uint32_t TILE = uint32_t(r.shape.tile());
 
   // ---- inputs on the device ----------------------------------------------
   const uint32_t* d_reads = reads;
@@ -259,17 +494,14 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
     h2d += pl.n_words * 4;
     d_reads = static_cast<const uint32_t*>(c->store.p);
   }
-  const uint32_t TILE = uint32_t(onesweep_shape(c->opt.tile_items).tile());
-  const uint64_t n_tiles = (pl.N + TILE - 1) / TILE;
   std::vector<uint32_t> len_bases;
   const uint64_t* d_desc = nullptr;
-  const uint32_t* d_lenhist = nullptr;
   if (!pl.uniform) {
     if (!hlens) {
       lens_copy.resize(n);
       CX_CUDA(c, cudaMemcpyAsync(lens_copy.data(), lens, n * 4, cudaMemcpyDeviceToHost, st));
       CX_CUDA(c, cudaStreamSynchronize(st));
-      d2h += n * 4;
+      r.d2h += n * 4;
       hlens = lens_copy.data();
     }
     std::vector<uint64_t> desc(n);
@@ -304,240 +536,207 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
     CX_CUDA(c, cudaMemcpyAsync(c->lenhist.p, lh.data(), (pl.Lmax + 1) * 4, cudaMemcpyHostToDevice, st));
     h2d += n * 8 + (pl.Lmax + 1) * 4;
     d_desc = static_cast<const uint64_t*>(c->desc.p);
-    d_lenhist = static_cast<const uint32_t*>(c->lenhist.p);
+  }
+  r.R = ReadIndex{d_reads, pl.n_words, d_desc, pl.shift, pl.uniform ? pl.Lmax : 0u, uint32_t(n),
+                  (reinterpret_cast<uintptr_t>(d_reads) & 15u) == 0 ? 1u : 0u};
+
+  // ---- outputs on the device ---------------------------------------------
+  const uint64_t bwt_words = (pl.N + 15) / 16;
+  r.d_bwt = out_bwt;
+  if (!bwt_dev) {
+    CX_TRY(ensure(c, c->out_bwt, bwt_words * 4, "BWT output"));
+    r.d_bwt = static_cast<uint32_t*>(c->out_bwt.p);
+  }
+  r.d_dollar = out_dollar;
+  if (out_dollar && !dollar_dev) {
+    CX_TRY(ensure(c, c->out_dollar, n * 8, "dollar positions"));
+    r.d_dollar = static_cast<uint64_t*>(c->out_dollar.p);
   }
 
+  // ---- slices --------------------------------------------------------------
+  // Device bytes per suffix of a slice: ids and keys (double-buffered),
+  // look-back words, group lists; plus the SA staging when it goes to the host.
+  const double per_row = 2.0 * pl.idb + 8.0 + 8.0 * kRadix / TILE + 8.0 / 33 + (out_sa && !sa_dev ? 8.0 : 0.0);
+  const uint64_t fixed = uint64_t(pl.Lmax) * kRadix * 4 + uint64_t(pl.D + pl.len_passes + 5) * kRadix * 4 +
+                         uint64_t(pl.W) * 4 * kRadix * 4 + (uint64_t(1) << kBucketBits) * 8 + (1u << 20);
+  // Buffers sized per slice are reused (or regrown) by this build: they do
+  // not count against what it may take.
+  const uint64_t reusable = c->vals[0].cap + c->vals[1].cap + c->keys[0].cap + c->keys[1].cap + c->status.cap +
+                            c->seglist.cap + c->out_sa.cap;
+  const uint64_t held_fixed = c->held - reusable;
+  const uint64_t avail = c->budget > held_fixed + fixed ? c->budget - held_fixed - fixed : 0;
+  uint64_t m1 = uint64_t(double(avail) / per_row);
+  // A slice must fit 32-bit row counts; every workspace buffer below is
+  // granted in 2 MB steps, so leave room for that rounding.
+  m1 = std::min<uint64_t>(m1 > (64u << 20) ? m1 - (1u << 20) : (m1 > 32768 ? m1 - 16384 : m1), 0xFFFFFFF0ull);
+  std::vector<Slice> slices;
+  if (pl.N <= m1) {
+    Slice sl;
+    sl.rows = uint32_t(pl.N);
+    slices.push_back(sl);
+  } else {
+    if (!pl.uniform)
+      return fail(c, CXBWT_EUNSUPPORTED, "collections of mixed read lengths must fit one slice (%llu suffixes, %llu fit)",
+                  (unsigned long long)pl.N, (unsigned long long)m1);
+    if (!pl.groups)
+      return fail(c, CXBWT_EUNSUPPORTED, "device-memory-bounded slices use the group plan (reads of at most 272 bases)");
+    // Figure 2 step 1: suffixes per bucket; then consecutive buckets packed
+    // into slices of at most m1 suffixes.
+    CX_TRY(ensure(c, c->bhist, (uint64_t(1) << kBucketBits) * 8, "bucket counts"));
+    CX_CUDA(c, cudaMemsetAsync(c->bhist.p, 0, (uint64_t(1) << kBucketBits) * 8, st));
+    CX_CUDA(c, launch_bucket_hist(r.R, uint32_t(n), kBucketBits, static_cast<unsigned long long*>(c->bhist.p),
+                                  c->sm_count, st));
+    ++r.launches;
+    std::vector<uint64_t> bh(size_t(1) << kBucketBits);
+    CX_CUDA(c, cudaMemcpyAsync(bh.data(), c->bhist.p, bh.size() * 8, cudaMemcpyDeviceToHost, st));
+    CX_CUDA(c, cudaStreamSynchronize(st));
+    r.d2h += bh.size() * 8;
+    uint64_t row = 0, acc = 0;
+    uint32_t lo = 0;
+    for (uint32_t b = 0; b <= bh.size(); ++b) {
+      const bool end = (b == bh.size());
+      const uint64_t cnt = end ? 0 : bh[b];
+      if (!end && cnt > m1)
+        return fail(c, CXBWT_ENOMEM, "one 8-base bucket holds %llu suffixes, more than the %llu a slice can hold",
+                    (unsigned long long)cnt, (unsigned long long)m1);
+      if (end || acc + cnt > m1) {
+        if (acc) {
+          Slice sl;
+          sl.whole = false;
+          sl.lo = lo;
+          sl.hi = b;
+          sl.rows = uint32_t(acc);
+          sl.row0 = row;
+          slices.push_back(sl);
+          row += acc;
+        }
+        lo = b;
+        acc = 0;
+      }
+      acc += cnt;
+    }
+    if (row != pl.N) return fail(c, CXBWT_EINTERNAL, "bucket counts sum to %llu, not N", (unsigned long long)row);
+    // Gathers walk the store in address order when it is too big for L2.
+    r.read_major = pl.Lmax <= 255 && (pl.n_words * 4 > (64u << 20) || (c->opt.plan_flags & CXBWT_PLAN_READ_MAJOR));
+    CX_CUDA(c, cudaMemsetAsync(r.d_bwt, 0, bwt_words * 4, st));  // slice edges are merged with atomicOr
+  }
+  uint32_t max_rows = 0;
+  for (const Slice& sl : slices) max_rows = std::max(max_rows, sl.rows);
+  const uint64_t gen_tiles = (pl.N + TILE - 1) / TILE;
+
   // ---- workspace ---------------------------------------------------------
-  CX_TRY(ensure(c, c->vals[0], pl.N * 4, "suffix ids"));
-  CX_TRY(ensure(c, c->vals[1], pl.N * 4, "suffix ids"));
-  CX_TRY(ensure(c, c->keys[0], pl.N * 4, "keys"));
-  CX_TRY(ensure(c, c->keys[1], pl.N * 4, "keys"));
+  CX_TRY(ensure(c, c->vals[0], uint64_t(max_rows) * pl.idb, "suffix ids"));
+  CX_TRY(ensure(c, c->vals[1], uint64_t(max_rows) * pl.idb, "suffix ids"));
+  CX_TRY(ensure(c, c->keys[0], uint64_t(max_rows) * 4, "keys"));
+  CX_TRY(ensure(c, c->keys[1], uint64_t(max_rows) * 4, "keys"));
   const void* status_before = c->status.p;
-  CX_TRY(ensure(c, c->status, n_tiles * kRadix * 8, "look-back words"));
+  CX_TRY(ensure(c, c->status, gen_tiles * kRadix * 8, "look-back words"));
   if (c->status.p != status_before) {
     // Fresh memory could hold any flag value: clear it so no stale word looks published.
     CX_CUDA(c, cudaMemsetAsync(c->status.p, 0, c->status.cap, st));
   }
   CX_TRY(ensure(c, c->P, uint64_t(pl.Lmax) * kRadix * 4, "position counts"));
-  CX_TRY(ensure(c, c->base, uint64_t(pl.D + pl.len_passes) * kRadix * 4, "digit bases"));
-  uint32_t* d_base = static_cast<uint32_t*>(c->base.p);
+  CX_TRY(ensure(c, c->base, uint64_t(std::max<uint32_t>(pl.D + pl.len_passes, 5)) * kRadix * 4, "digit bases"));
+  if (pl.uniform && !c->lenhist.p) CX_TRY(ensure(c, c->lenhist, 4, "length histogram"));
+  if (pl.groups && pl.Lmax > 16) {
+    CX_TRY(ensure(c, c->seglist, (uint64_t(max_rows) / 33 + 1 + uint64_t(max_rows) / kCtaMax + 1) * 8, "group lists"));
+    CX_TRY(ensure(c, c->rhist, size_t(pl.W) * 4 * kRadix * 4, "group digit counts"));
+  }
+  r.d_sa = out_sa;
+  if (out_sa && !sa_dev) {
+    CX_TRY(ensure(c, c->out_sa, uint64_t(max_rows) * 8, "suffix array slice"));
+    r.d_sa = static_cast<uint64_t*>(c->out_sa.p);
+  }
+  r.vals[0] = c->vals[0].p;
+  r.vals[1] = c->vals[1].p;
+  r.keys[0] = static_cast<uint32_t*>(c->keys[0].p);
+  r.keys[1] = static_cast<uint32_t*>(c->keys[1].p);
+  r.base = static_cast<uint32_t*>(c->base.p);
   if (pl.len_passes) {
-    CX_CUDA(c, cudaMemcpyAsync(d_base + size_t(pl.D) * kRadix, len_bases.data(), len_bases.size() * 4,
+    CX_CUDA(c, cudaMemcpyAsync(r.base + size_t(pl.D) * kRadix, len_bases.data(), len_bases.size() * 4,
                                cudaMemcpyHostToDevice, st));
     h2d += len_bases.size() * 4;
   }
-  const uint32_t passes = pl.D + pl.len_passes;
-  if (uint64_t(c->epoch) + passes + 2 >= (uint64_t(1) << 30)) {
+  const uint64_t passes_max = uint64_t(slices.size()) * (pl.D + pl.len_passes + 1) + 4 * pl.W * 64;
+  if (uint64_t(c->epoch) + passes_max + 2 >= (uint64_t(1) << 30)) {
     // Look-back flags are 2*epoch and 2*epoch+1 in 32 bits: restart the epochs.
     CX_CUDA(c, cudaMemsetAsync(c->status.p, 0, c->status.cap, st));
     c->epoch = 0;
   }
-  CX_CUDA(c, cudaMemsetAsync(c->P.p, 0, uint64_t(pl.Lmax) * kRadix * 4, st));
-  CX_CUDA(c, cudaMemsetAsync(d_counts, 0, 5 * 8, st));
+  CX_CUDA(c, cudaMemsetAsync(r.d_counts, 0, 5 * 8, st));
 
   const bool timing = c->opt.timing != 0;
   if (timing) CX_CUDA(c, cudaEventRecord(c->ev[0], st));
-
-  ReadIndex R{d_reads, pl.n_words, d_desc, pl.shift, pl.uniform ? pl.Lmax : 0u, uint32_t(n),
-              (reinterpret_cast<uintptr_t>(d_reads) & 15u) == 0 ? 1u : 0u};
-
-  // ---- 1. all-digit histogram -----------------------------------------------
-  CX_CUDA(c, launch_poscount(R, uint32_t(n), pl.Lmax, static_cast<uint32_t*>(c->P.p), c->sm_count, st));
-  CX_CUDA(c, launch_digitbase(static_cast<const uint32_t*>(c->P.p), pl.Lmax, d_sorted, pl.uniform ? 1 : 0,
-                              uint32_t(n), pl.Lmax, d_lenhist, d_base, st));
-  launches += 2;
-
-  // ---- 2./3. digit passes ----------------------------------------------------
-  uint32_t* vals[2] = {static_cast<uint32_t*>(c->vals[0].p), static_cast<uint32_t*>(c->vals[1].p)};
-  uint32_t* keys[2] = {static_cast<uint32_t*>(c->keys[0].p), static_cast<uint32_t*>(c->keys[1].p)};
-  int cur = 0, kin = 0;
-  const TileShape shape = onesweep_shape(c->opt.tile_items);
-  PassArgs a{};
-  a.status = static_cast<unsigned long long*>(c->status.p);
-  a.tile_counter = d_counter;
-  a.err = d_err;
-  a.R = R;
-  a.n_items = uint32_t(pl.N);
-  a.n_tiles = uint32_t(n_tiles);
-  a.n_reads = uint32_t(n);
-  a.timeout_ns = kTimeoutNs;
-
-  if (!pl.uniform) {
-    CX_CUDA(c, launch_identity(R, uint32_t(n), nullptr, vals[0], st));
-    ++launches;
-  }
   if (timing) CX_CUDA(c, cudaEventRecord(c->ev[1], st));
-  uint64_t sort_launches = 0, sort_items = 0;
-  for (uint32_t j = 0; j < pl.len_passes; ++j) {
-    a.vals_in = vals[cur];
-    a.vals_out = vals[cur ^ 1];
-    a.keys_in = nullptr;
-    a.keys_out = nullptr;
-    a.digit_base = d_base + size_t(pl.D + j) * kRadix;
-    a.key_shift = 8 * j;
-    a.window_c0 = 0;
-    a.epoch = ++c->epoch;
-    CX_CUDA(c, launch_onesweep(a, kSrcLength, false, shape, st));
-    cur ^= 1;
-    ++sort_launches;
-    sort_items += pl.N;
-  }
-  bool first = pl.uniform;
-  for (int64_t w = int64_t(w_last); w >= 0; --w) {
-    const uint32_t d_lo = uint32_t(4 * w);
-    const uint32_t d_hi = std::min<uint32_t>(d_lo + 3, pl.D - 1);
-    for (int64_t d = d_hi; d >= int64_t(d_lo); --d) {
-      const bool first_in_window = (uint32_t(d) == d_hi);
-      const bool last_in_window = (uint32_t(d) == d_lo);
-      const int mode = first_in_window ? (first ? kSrcInitUniform : kSrcExtract) : kSrcCarried;
-      // The group plan keeps the window-0 keys of the final order: groups are runs of equal keys.
-      const bool write_key = !last_in_window || groups;
-      a.vals_in = vals[cur];
-      a.vals_out = vals[cur ^ 1];
-      a.keys_in = (mode == kSrcCarried) ? keys[kin] : nullptr;
-      const int kout = (mode == kSrcCarried) ? (kin ^ 1) : kin;
-      a.keys_out = write_key ? keys[kout] : nullptr;
-      a.digit_base = d_base + size_t(d) * kRadix;
-      a.key_shift = 24u - 8u * uint32_t(d - d_lo);
-      a.window_c0 = uint32_t(16 * w);
-      a.epoch = ++c->epoch;
-      CX_CUDA(c, launch_onesweep(a, mode, write_key, shape, st));
-      cur ^= 1;
-      if (write_key) kin = kout;
-      first = false;
-      ++sort_launches;
-      sort_items += pl.N;
-    }
-  }
-  if (timing) CX_CUDA(c, cudaEventRecord(c->ev[2], st));
-  launches += sort_launches;
 
-  // ---- 3b. group plan: finish every group of equal first windows on chip ------
-  if (groups && pl.Lmax > 16) {
-    const uint64_t cta_cap = pl.N / 33 + 1, big_cap = pl.N / kCtaMax + 1;
-    CX_TRY(ensure(c, c->seglist, (cta_cap + big_cap) * 8, "group lists"));
-    auto* d_seg = reinterpret_cast<uint32_t*>(misc + kMiscSeg);
-    CX_CUDA(c, cudaMemsetAsync(d_seg, 0, 16, st));
-    SegArgs g{};
-    g.keys = keys[kin];
-    g.vals = vals[cur];
-    g.n_items = uint32_t(pl.N);
-    g.R = R;
-    g.depth = 16;
-    g.cta_list = static_cast<uint2*>(c->seglist.p);
-    g.cta_cap = uint32_t(cta_cap);
-    g.big_list = g.cta_list + cta_cap;
-    g.big_cap = uint32_t(big_cap);
-    g.counts = d_seg;
-    g.err = d_err;
-    CX_CUDA(c, launch_segsort(g, seg_words, c->sm_count, st));
-    launches += 2;
-    // Remainders too large for one CTA (rare: long runs of equal bases) are
-    // finished here with LSD passes over bases 16.. restricted to their rows.
-    CX_CUDA(c, cudaMemcpyAsync(c->h_small + 5, d_seg, 8, cudaMemcpyDeviceToHost, st));
-    CX_CUDA(c, cudaStreamSynchronize(st));
-    const uint32_t n_big = std::min<uint32_t>(reinterpret_cast<const uint32_t*>(c->h_small + 5)[1], g.big_cap);
-    if (n_big) {
-      std::vector<uint2> big(n_big);
-      CX_CUDA(c, cudaMemcpyAsync(big.data(), g.big_list, n_big * 8, cudaMemcpyDeviceToHost, st));
-      CX_CUDA(c, cudaStreamSynchronize(st));
-      d2h += n_big * 8;
-      const uint32_t n_win = pl.W - 1;
-      CX_TRY(ensure(c, c->rhist, size_t(n_win) * 4 * kRadix * 4, "group digit counts"));
-      auto* rh = static_cast<uint32_t*>(c->rhist.p);
-      for (const uint2& bg : big) {
-        const uint32_t s0 = bg.x, m = bg.y;
-        CX_CUDA(c, cudaMemsetAsync(rh, 0, size_t(n_win) * 4 * kRadix * 4, st));
-        CX_CUDA(c, launch_range_hist(vals[cur] + s0, m, R, n_win, rh, c->sm_count, st));
-        launches += 2;
-        uint32_t* gv[2] = {vals[cur] + s0, vals[cur ^ 1] + s0};
-        uint32_t* gk[2] = {keys[0] + s0, keys[1] + s0};
-        int gc = 0, gki = 0;
-        PassArgs b = a;
-        b.n_items = m;
-        b.n_tiles = uint32_t((m + TILE - 1) / TILE);
-        for (uint32_t w = pl.W - 1; w >= 1; --w) {
-          const uint32_t d_lo = 4 * w;
-          const uint32_t d_hi = std::min<uint32_t>(d_lo + 3, pl.D - 1);
-          for (int64_t d = d_hi; d >= int64_t(d_lo); --d) {
-            const bool first_in_window = (uint32_t(d) == d_hi);
-            const bool last_in_window = (uint32_t(d) == d_lo);
-            const int mode = first_in_window ? kSrcExtract : kSrcCarried;
-            const bool write_key = !last_in_window;
-            b.vals_in = gv[gc];
-            b.vals_out = gv[gc ^ 1];
-            b.keys_in = (mode == kSrcCarried) ? gk[gki] : nullptr;
-            const int kout = (mode == kSrcCarried) ? (gki ^ 1) : gki;
-            b.keys_out = write_key ? gk[kout] : nullptr;
-            b.digit_base = rh + size_t((w - 1) * 4 + (uint32_t(d) - d_lo)) * kRadix;
-            b.key_shift = 24u - 8u * (uint32_t(d) - d_lo);
-            b.window_c0 = 16 * w;
-            b.epoch = ++c->epoch;
-            CX_CUDA(c, launch_onesweep(b, mode, write_key, shape, st));
-            gc ^= 1;
-            if (write_key) gki = kout;
-            ++launches;
-            ++sort_launches;
-            sort_items += m;
-          }
-        }
-        if (gc) CX_CUDA(c, cudaMemcpyAsync(gv[0], gv[1], size_t(m) * 4, cudaMemcpyDeviceToDevice, st));
+  uint64_t words_sent = 0;  // BWT words already streamed to the host
+  for (size_t si = 0; si < slices.size(); ++si) {
+    const Slice& sl = slices[si];
+    int cur = 0;
+    CX_TRY(sort_slice(c, r, sl, &cur));
+    if (timing && si + 1 == slices.size()) CX_CUDA(c, cudaEventRecord(c->ev[4], st));
+    // ---- emission of the slice -------------------------------------------
+    EmitArgs e{};
+    e.sa = r.vals[cur];
+    e.n = sl.rows;
+    e.row0 = sl.row0;
+    e.n_total = pl.N;
+    e.R = r.R;
+    e.bwt = r.d_bwt;
+    e.word_base = 0;
+    e.dollar_pos = r.d_dollar;
+    e.counts = r.d_counts;
+    e.sa_out = r.d_sa ? (sa_dev ? r.d_sa + sl.row0 : r.d_sa) : nullptr;
+    e.err = r.d_err;
+    e.id_bytes = pl.idb;
+    CX_CUDA(c, launch_emit(e, st));
+    ++r.launches;
+    if (out_sa && !sa_dev) {
+      CX_CUDA(c, cudaMemcpyAsync(out_sa + sl.row0, r.d_sa, uint64_t(sl.rows) * 8, cudaMemcpyDeviceToHost, st));
+      r.d2h += uint64_t(sl.rows) * 8;
+    }
+    if (!bwt_dev) {
+      // Words whose 16 rows are all emitted stream to the host while the next slice sorts.
+      const bool last = si + 1 == slices.size();
+      const uint64_t done = last ? bwt_words : (sl.row0 + sl.rows) / 16;
+      if (done > words_sent) {
+        cudaEvent_t ev = c->slice_done[si & 1];
+        CX_CUDA(c, cudaEventRecord(ev, st));
+        CX_CUDA(c, cudaStreamWaitEvent(c->side, ev, 0));
+        CX_CUDA(c, cudaMemcpyAsync(out_bwt + words_sent, r.d_bwt + words_sent, (done - words_sent) * 4,
+                                   cudaMemcpyDeviceToHost, c->side));
+        r.d2h += (done - words_sent) * 4;
+        words_sent = done;
       }
     }
   }
-
-  if (timing) CX_CUDA(c, cudaEventRecord(c->ev[4], st));
-
-  // ---- 4. emission -----------------------------------------------------------
-  const uint64_t bwt_words = (pl.N + 15) / 16;
-  uint32_t* d_bwt = out_bwt;
-  if (!bwt_dev) {
-    CX_TRY(ensure(c, c->out_bwt, bwt_words * 4, "BWT output"));
-    d_bwt = static_cast<uint32_t*>(c->out_bwt.p);
-  }
-  uint64_t* d_dollar = out_dollar;
-  if (out_dollar && !dollar_dev) {
-    CX_TRY(ensure(c, c->out_dollar, n * 8, "dollar positions"));
-    d_dollar = static_cast<uint64_t*>(c->out_dollar.p);
-  }
-  uint64_t* d_sa = out_sa;
-  if (out_sa && !sa_dev) {
-    CX_TRY(ensure(c, c->out_sa, pl.N * 8, "suffix array output"));
-    d_sa = static_cast<uint64_t*>(c->out_sa.p);
-  }
-  EmitArgs e{vals[cur], uint32_t(pl.N), R, d_bwt, d_dollar, d_counts, d_sa, d_err};
-  CX_CUDA(c, launch_emit(e, st));
-  ++launches;
-  if (out_counts) {
-    CX_CUDA(c, cudaMemcpyAsync(out_counts, d_counts, 5 * 8, counts_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                               st));
-    if (!counts_dev) d2h += 40;
-  }
   if (timing) CX_CUDA(c, cudaEventRecord(c->ev[3], st));
   if (!bwt_dev) {
-    CX_CUDA(c, cudaMemcpyAsync(out_bwt, d_bwt, bwt_words * 4, cudaMemcpyDeviceToHost, st));
-    d2h += bwt_words * 4;
+    CX_CUDA(c, cudaEventRecord(c->slice_done[0], c->side));
+    CX_CUDA(c, cudaStreamWaitEvent(st, c->slice_done[0], 0));
+  }
+  if (out_counts) {
+    CX_CUDA(c, cudaMemcpyAsync(out_counts, r.d_counts, 5 * 8, counts_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                               st));
+    if (!counts_dev) r.d2h += 40;
   }
   if (out_dollar && !dollar_dev) {
-    CX_CUDA(c, cudaMemcpyAsync(out_dollar, d_dollar, n * 8, cudaMemcpyDeviceToHost, st));
-    d2h += n * 8;
+    CX_CUDA(c, cudaMemcpyAsync(out_dollar, r.d_dollar, n * 8, cudaMemcpyDeviceToHost, st));
+    r.d2h += n * 8;
   }
-  if (out_sa && !sa_dev) {
-    CX_CUDA(c, cudaMemcpyAsync(out_sa, d_sa, pl.N * 8, cudaMemcpyDeviceToHost, st));
-    d2h += pl.N * 8;
-  }
-  CX_CUDA(c, cudaMemcpyAsync(c->h_small + 4, d_err, 4, cudaMemcpyDeviceToHost, st));
+  CX_CUDA(c, cudaMemcpyAsync(c->h_small + 4, r.d_err, 4, cudaMemcpyDeviceToHost, st));
 
-  c->stats.kernel_launches += launches;
-  c->stats.sort_pass_launches += sort_launches;
-  c->stats.sort_pass_items += sort_items;
+  c->stats.kernel_launches += r.launches + r.sort_launches;
+  c->stats.sort_pass_launches += r.sort_launches;
+  c->stats.sort_pass_items += r.sort_items;
   c->stats.h2d_bytes += h2d;
-  c->stats.d2h_bytes += d2h;
+  c->stats.d2h_bytes += r.d2h;
   c->stats.device_bytes_held = c->held;
+  c->stats.slices += slices.size();
 
   const bool host_out = !bwt_dev || (out_dollar && !dollar_dev) || (out_counts && !counts_dev) || (out_sa && !sa_dev);
   if (c->opt.async && !host_out) {
-    // Completed (and checked) by the next call on this context or cxbwt_sync.
+    // Completed (and checked) by cxbwt_sync.
     c->stats.builds += 1;
     c->stats.bases += pl.sum;
     c->stats.suffixes += pl.N;
@@ -547,10 +746,12 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   CX_TRY(take_device_error(c));
   if (timing) {
     float ms_sort = 0, ms_all = 0, ms_group = 0, ms_emit = 0;
-    CX_CUDA(c, cudaEventElapsedTime(&ms_sort, c->ev[1], c->ev[2]));
-    CX_CUDA(c, cudaEventElapsedTime(&ms_group, c->ev[2], c->ev[4]));
-    CX_CUDA(c, cudaEventElapsedTime(&ms_emit, c->ev[4], c->ev[3]));
     CX_CUDA(c, cudaEventElapsedTime(&ms_all, c->ev[0], c->ev[3]));
+    if (slices.size() == 1) {
+      CX_CUDA(c, cudaEventElapsedTime(&ms_sort, c->ev[1], c->ev[2]));
+      CX_CUDA(c, cudaEventElapsedTime(&ms_group, c->ev[2], c->ev[4]));
+      CX_CUDA(c, cudaEventElapsedTime(&ms_emit, c->ev[4], c->ev[3]));
+    }
     c->stats.sort_pass_ms += ms_sort;
     c->stats.group_ms += ms_group;
     c->stats.emit_ms += ms_emit;
@@ -614,6 +815,8 @@ int cxbwt_create(cxbwt_ctx** out, const cxbwt_options* opt) {
   c->budget = o.device_budget_bytes ? o.device_budget_bytes : uint64_t(double(free_b) * 0.9);
   bool ok = cudaMallocHost(reinterpret_cast<void**>(&c->h_small), 64) == cudaSuccess;
   for (auto& ev : c->ev) ok = ok && cudaEventCreate(&ev) == cudaSuccess;
+  for (auto& ev : c->slice_done) ok = ok && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess;
   if (ok) ok = ensure(c, c->misc, kMiscBytes, "scratch words") == CXBWT_OK;
   if (ok) ok = cudaMemset(c->misc.p, 0, kMiscBytes) == cudaSuccess;
   if (!ok) {
@@ -632,10 +835,13 @@ void cxbwt_destroy(cxbwt_ctx* c) {
   cudaDeviceSynchronize();
   DevBuf* bufs[] = {&c->vals[0], &c->vals[1], &c->keys[0], &c->keys[1], &c->status, &c->P, &c->base,
                     &c->lenhist, &c->desc, &c->misc, &c->store, &c->out_bwt, &c->out_dollar, &c->out_sa,
-                    &c->seglist, &c->rhist};
+                    &c->seglist, &c->rhist, &c->bhist};
   for (DevBuf* b : bufs) release(c, *b);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
+  for (auto& ev : c->slice_done)
+    if (ev) cudaEventDestroy(ev);
+  if (c->side) cudaStreamDestroy(c->side);
   if (c->h_small) cudaFreeHost(c->h_small);
   delete c;
 }

@@ -1,8 +1,8 @@
 // Device-side building blocks shared by the cxbwt kernels.
 //
 // Suffix encoding.  A suffix S_i[k..] $_i is carried through the sort as one
-// 32-bit value v = (i << shift) | k, with 2^shift > max L_i so that k in
-// [0, L_i] fits.  Moving these values instead of the suffixes is the paper's
+// id v = (i << shift) | k, with 2^shift > max L_i so that k in [0, L_i]
+// fits; the id is 32 bits while n * 2^shift < 2^32, else 64 bits.  Moving these values instead of the suffixes is the paper's
 // "sort by index" (Section 3.2).
 //
 // Read store.  Bases are 2-bit codes, most significant first, reads
@@ -45,10 +45,11 @@ struct Suffix {
   uint32_t read; // i
 };
 
-__device__ __forceinline__ Suffix decode(const ReadIndex& R, uint32_t v) {
+template <class V>
+__device__ __forceinline__ Suffix decode(const ReadIndex& R, V v) {
   Suffix s;
-  s.read = v >> R.shift;
-  s.k = v & ((1u << R.shift) - 1u);
+  s.read = uint32_t(v >> R.shift);
+  s.k = uint32_t(v) & ((1u << R.shift) - 1u);
   if (R.desc) {
     // The clamp only matters for a corrupted value; it keeps the load in bounds.
     const uint64_t d = __ldg(R.desc + min(s.read, R.n_reads - 1u));

@@ -10,7 +10,7 @@ constexpr uint32_t kCtaMax = 2048;  // largest group remainder finished by one C
 
 struct SegArgs {
   const uint32_t* keys;   // first 16-base window of each row, ascending
-  uint32_t* vals;         // suffix ids, sorted by that window; finished in place
+  void* vals;             // suffix ids (uint32 or uint64), sorted by that window; finished in place
   uint32_t n_items;
   ReadIndex R;
   uint32_t depth;         // bases already sorted (16)
@@ -25,9 +25,9 @@ struct SegArgs {
 // Key words a group remainder is sorted by for reads of at most max_len bases
 // (a compiled width >= ceil((max_len - 16) / 16)), or 0 if too long.
 int segsort_words(uint32_t max_len);
-cudaError_t launch_segsort(const SegArgs& a, int nw, int sm_count, cudaStream_t st);
+cudaError_t launch_segsort(const SegArgs& a, int nw, int id_bytes, int sm_count, cudaStream_t st);
 // Digit bases (exclusive, per digit position) of windows 1 .. n_win over n rows of vals.
-cudaError_t launch_range_hist(const uint32_t* vals, uint32_t n, const ReadIndex& R, uint32_t n_win, uint32_t* hist,
-                              int sm_count, cudaStream_t st);
+cudaError_t launch_range_hist(const void* vals, int id_bytes, uint32_t n, const ReadIndex& R, uint32_t n_win,
+                              uint32_t* hist, int sm_count, cudaStream_t st);
 
 }  // namespace cxbwt

@@ -92,7 +92,8 @@ __device__ __forceinline__ bool key_less(const uint32_t (&a)[NW], uint32_t pa, c
   return pa < pb;
 }
 
-__device__ __forceinline__ uint32_t suffix_len(const ReadIndex& R, uint32_t v) {
+template <class V>
+__device__ __forceinline__ uint32_t suffix_len(const ReadIndex& R, V v) {
   const Suffix s = decode(R, v);
   return s.len - s.k;
 }
@@ -109,17 +110,18 @@ struct RowWords {
   uint4 r[32][kStride / 4];
 };
 
-template <int NW>
+template <int NW, class V>
 __device__ void warp_rank_window(const SegArgs& a, uint32_t cur, uint32_t n_rows, uint32_t gid, uint32_t gend,
                                  bool need, int lane, RowWords<NW>& sw) {
   constexpr int Q = RowWords<NW>::kStride / 4;
+  V* vals = static_cast<V*>(a.vals);
   const bool live = uint32_t(lane) < n_rows;
   uint32_t w[Q * 4];
-  uint32_t v = 0;
+  V v = 0;
 #pragma unroll
   for (int i = 0; i < Q * 4; ++i) w[i] = 0u;
   if (live) {
-    v = a.vals[cur + lane];
+    v = vals[cur + lane];
     if (need) {
       uint32_t g[NW];
       gather_words<NW>(a.R, decode(a.R, v), a.depth, g);
@@ -151,7 +153,7 @@ __device__ void warp_rank_window(const SegArgs& a, uint32_t cur, uint32_t n_rows
     rank += lt ? 1u : 0u;
   }
   __syncwarp();  // every lane has read its row and the shared words before any overwrite
-  if (live && gid + rank != uint32_t(lane)) a.vals[cur + gid + rank] = v;
+  if (live && gid + rank != uint32_t(lane)) vals[cur + gid + rank] = v;
 }
 
 // First row r >= from (r < n) whose window differs from row r-1, or n.
@@ -177,17 +179,18 @@ __device__ uint32_t next_head(const SegArgs& a, uint32_t from, int lane) {
 
 // Finish one group of more than 32 rows [gs, ge): skip its finished prefix,
 // sort a remainder of at most 32 rows here, list a larger one.
-template <int NW>
+template <int NW, class V>
 __device__ void finish_long_group(const SegArgs& a, uint32_t gs, uint32_t ge, int lane, RowWords<NW>& sw) {
+  const V* vals = static_cast<const V*>(a.vals);
   uint32_t lo = gs, hi = ge;
   while (lo < hi) {
     const uint32_t mid = lo + (hi - lo) / 2;
-    if (suffix_len(a.R, a.vals[mid]) > a.depth) hi = mid; else lo = mid + 1;
+    if (suffix_len(a.R, vals[mid]) > a.depth) hi = mid; else lo = mid + 1;
   }
   const uint32_t m = ge - lo;
   if (m < 2) return;
   if (m <= 32) {
-    warp_rank_window<NW>(a, lo, m, 0u, m, true, lane, sw);
+    warp_rank_window<NW, V>(a, lo, m, 0u, m, true, lane, sw);
   } else if (lane == 0) {
     const bool cta = m <= kCtaMax;
     const uint32_t slot = atomicAdd(a.counts + (cta ? 0 : 1), 1u);
@@ -198,7 +201,7 @@ __device__ void finish_long_group(const SegArgs& a, uint32_t gs, uint32_t ge, in
 
 // Each warp owns the groups whose first row lies in its chunk of kChunk rows
 // and walks them in windows of up to 32 rows made of whole groups.
-template <int NW>
+template <int NW, class V>
 __global__ void __launch_bounds__(256) k_segsort_warp(const SegArgs a) {
   const int lane = threadIdx.x & 31;
   __shared__ RowWords<NW> s_rows[8];
@@ -220,7 +223,7 @@ __global__ void __launch_bounds__(256) k_segsort_warp(const SegArgs a) {
       if (past) hm &= (past & (~past + 1)) * 2u - 1u;  // keep bits up to the lowest one in past
       if (hm == 0) {  // the group at cur has more than 32 rows
         const uint32_t ge = next_head(a, cur + 33, lane);
-        finish_long_group<NW>(a, cur, ge, lane, sw);
+        finish_long_group<NW, V>(a, cur, ge, lane, sw);
         cur = ge;
         continue;
       }
@@ -235,7 +238,7 @@ __global__ void __launch_bounds__(256) k_segsort_warp(const SegArgs a) {
         const uint32_t gid = 31u - __clz(upto);
         const uint32_t after = lane == 31 ? 0u : (heads_at & ~((2u << lane) - 1u));
         const uint32_t gend = after ? min(uint32_t(__ffs(after) - 1), n_rows) : n_rows;
-        warp_rank_window<NW>(a, cur, n_rows, gid, gend, gend - gid > 1, lane, sw);
+        warp_rank_window<NW, V>(a, cur, n_rows, gid, gend, gend - gid > 1, lane, sw);
       }
       cur += n_rows;
     }
@@ -243,12 +246,13 @@ __global__ void __launch_bounds__(256) k_segsort_warp(const SegArgs a) {
 }
 
 // Shared-memory bitonic sort of one listed group per CTA (33 .. kCtaMax members).
-template <int NW>
+template <int NW, class V>
 __global__ void __launch_bounds__(512) k_segsort_cta(const SegArgs a) {
   extern __shared__ __align__(16) uint32_t sm[];
-  uint32_t* s_w = sm;                       // [NW][kCtaMax]
-  uint32_t* s_v = sm + NW * kCtaMax;        // [kCtaMax]
-  uint16_t* s_perm = reinterpret_cast<uint16_t*>(s_v + kCtaMax);  // [kCtaMax]
+  V* vals = static_cast<V*>(a.vals);
+  V* s_v = reinterpret_cast<V*>(sm);                                  // [kCtaMax]
+  uint32_t* s_w = reinterpret_cast<uint32_t*>(s_v + kCtaMax);         // [NW][kCtaMax]
+  uint16_t* s_perm = reinterpret_cast<uint16_t*>(s_w + NW * kCtaMax);  // [kCtaMax]
   __shared__ uint32_t s_item;
   const uint32_t n_list = min(*(volatile uint32_t*)(a.counts + 0), a.cta_cap);
   for (;;) {
@@ -264,7 +268,7 @@ __global__ void __launch_bounds__(512) k_segsort_cta(const SegArgs a) {
     for (uint32_t x = threadIdx.x; x < P; x += blockDim.x) {
       s_perm[x] = uint16_t(x);
       if (x < m) {
-        const uint32_t v = a.vals[s + x];
+        const V v = vals[s + x];
         uint32_t w[NW];
         gather_words<NW>(a.R, decode(a.R, v), a.depth, w);
 #pragma unroll
@@ -304,14 +308,15 @@ __global__ void __launch_bounds__(512) k_segsort_cta(const SegArgs a) {
         __syncthreads();
       }
     }
-    for (uint32_t x = threadIdx.x; x < m; x += blockDim.x) a.vals[s + x] = s_v[s_perm[x]];
+    for (uint32_t x = threadIdx.x; x < m; x += blockDim.x) vals[s + x] = s_v[s_perm[x]];
   }
 }
 
 // Digit counts of bases [16, 16 * (1 + NWIN)) over rows [0, n) of vals: the
 // per-pass histograms of the LSD passes that finish one big group.
 // hist[(w * 4 + j) * 256 + digit] for window w (bases 16(w+1) ..) and digit j.
-__global__ void k_range_hist(const uint32_t* vals, uint32_t n, ReadIndex R, uint32_t n_win, uint32_t* hist) {
+template <class V>
+__global__ void k_range_hist(const V* vals, uint32_t n, ReadIndex R, uint32_t n_win, uint32_t* hist) {
   extern __shared__ uint32_t sh[];
   const uint32_t bins = n_win * 4 * kRadix;
   for (uint32_t x = threadIdx.x; x < bins; x += blockDim.x) sh[x] = 0;
@@ -347,25 +352,38 @@ __global__ void __launch_bounds__(kRadix) k_scan256(uint32_t* hist) {
   hist[row * kRadix + v] = s[v];
 }
 
-template <int NW>
+template <int NW, class V>
 cudaError_t launch_nw(const SegArgs& a, int sm_count, cudaStream_t st) {
   const uint32_t n_chunks = (a.n_items + kChunk - 1) / kChunk;
   uint32_t blocks = (n_chunks + 7) / 8;
   const uint32_t cap = uint32_t(sm_count) * 16;
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
-  k_segsort_warp<NW><<<blocks, 256, 0, st>>>(a);
+  k_segsort_warp<NW, V><<<blocks, 256, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t smem = size_t(NW + 1) * kCtaMax * 4 + kCtaMax * 2;
+  const size_t smem = size_t(kCtaMax) * (sizeof(V) + NW * 4 + 2);
   static bool configured = false;
   if (!configured) {
-    e = cudaFuncSetAttribute(k_segsort_cta<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    e = cudaFuncSetAttribute(k_segsort_cta<NW, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  k_segsort_cta<NW><<<sm_count * 2, 512, smem, st>>>(a);
+  k_segsort_cta<NW, V><<<sm_count * 2, 512, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+template <class V>
+cudaError_t launch_v(const SegArgs& a, int nw, int sm_count, cudaStream_t st) {
+  switch (nw) {
+    case 2: return launch_nw<2, V>(a, sm_count, st);
+    case 4: return launch_nw<4, V>(a, sm_count, st);
+    case 6: return launch_nw<6, V>(a, sm_count, st);
+    case 8: return launch_nw<8, V>(a, sm_count, st);
+    case 12: return launch_nw<12, V>(a, sm_count, st);
+    case 16: return launch_nw<16, V>(a, sm_count, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
@@ -382,27 +400,26 @@ int segsort_words(uint32_t max_len) {
   return 0;  // reads too long for the on-chip finish
 }
 
-cudaError_t launch_segsort(const SegArgs& a, int nw, int sm_count, cudaStream_t st) {
-  switch (nw) {
-    case 2: return launch_nw<2>(a, sm_count, st);
-    case 4: return launch_nw<4>(a, sm_count, st);
-    case 6: return launch_nw<6>(a, sm_count, st);
-    case 8: return launch_nw<8>(a, sm_count, st);
-    case 12: return launch_nw<12>(a, sm_count, st);
-    case 16: return launch_nw<16>(a, sm_count, st);
-    default: return cudaErrorInvalidValue;
-  }
+cudaError_t launch_segsort(const SegArgs& a, int nw, int id_bytes, int sm_count, cudaStream_t st) {
+  return id_bytes == 8 ? launch_v<uint64_t>(a, nw, sm_count, st) : launch_v<uint32_t>(a, nw, sm_count, st);
 }
 
-cudaError_t launch_range_hist(const uint32_t* vals, uint32_t n, const ReadIndex& R, uint32_t n_win, uint32_t* hist,
-                              int sm_count, cudaStream_t st) {
+cudaError_t launch_range_hist(const void* vals, int id_bytes, uint32_t n, const ReadIndex& R, uint32_t n_win,
+                              uint32_t* hist, int sm_count, cudaStream_t st) {
   if (n == 0 || n_win == 0) return cudaSuccess;
   const size_t smem = size_t(n_win) * 4 * kRadix * 4;
-  cudaError_t e = cudaFuncSetAttribute(k_range_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
   uint32_t blocks = (n + 255) / 256;
   if (blocks > uint32_t(sm_count) * 2) blocks = sm_count * 2;
-  k_range_hist<<<blocks, 256, smem, st>>>(vals, n, R, n_win, hist);
+  cudaError_t e;
+  if (id_bytes == 8) {
+    e = cudaFuncSetAttribute(k_range_hist<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    k_range_hist<uint64_t><<<blocks, 256, smem, st>>>(static_cast<const uint64_t*>(vals), n, R, n_win, hist);
+  } else {
+    e = cudaFuncSetAttribute(k_range_hist<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    k_range_hist<uint32_t><<<blocks, 256, smem, st>>>(static_cast<const uint32_t*>(vals), n, R, n_win, hist);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_scan256<<<n_win * 4, kRadix, 0, st>>>(hist);

@@ -23,6 +23,21 @@ namespace {
 constexpr int kSlab = 64;            // read positions per CTA slab: 64 x 256 counters = 64 KB
 constexpr int kCountThreads = 512;
 
+__device__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* scratch /*[blockDim/32]*/) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t incl = x;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) scratch[warp] = incl;
+  __syncthreads();
+  uint32_t pre = 0;
+  for (int w = 0; w < nw; ++w)
+    if (w < warp) pre += scratch[w];
+  return pre + incl - x;
+}
+
 __global__ void __launch_bounds__(kCountThreads) k_poscount(const ReadIndex R, uint32_t n_reads, uint32_t q_max,
                                                             uint32_t* __restrict__ P) {
   extern __shared__ uint32_t sP[];
@@ -31,7 +46,7 @@ __global__ void __launch_bounds__(kCountThreads) k_poscount(const ReadIndex R, u
   for (uint32_t x = threadIdx.x; x < qn * kRadix; x += blockDim.x) sP[x] = 0u;
   __syncthreads();
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n_reads; r += gridDim.x * blockDim.x) {
-    Suffix s = decode(R, r << R.shift);  // whole read (k = 0)
+    Suffix s = decode(R, uint64_t(r) << R.shift);  // whole read (k = 0)
     const uint32_t qe = min(q0 + qn, s.len);
     for (uint32_t q = q0; q < qe; q += 16) {
       // Bases q .. q+31 (A-padded): every 4-mer starting in q .. q+15.
@@ -48,21 +63,6 @@ __global__ void __launch_bounds__(kCountThreads) k_poscount(const ReadIndex R, u
     const uint32_t v = sP[x];
     if (v) atomicAdd(&P[uint64_t(q0) * kRadix + x], v);
   }
-}
-
-__device__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* scratch /*[blockDim/32]*/) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  uint32_t incl = x;
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) scratch[warp] = incl;
-  __syncthreads();
-  uint32_t pre = 0;
-  for (int w = 0; w < nw; ++w)
-    if (w < warp) pre += scratch[w];
-  return pre + incl - x;
 }
 
 __global__ void __launch_bounds__(kRadix) k_digitbase(const uint32_t* __restrict__ P, uint32_t q_max, int uniform,
@@ -91,15 +91,78 @@ __global__ void __launch_bounds__(kRadix) k_digitbase(const uint32_t* __restrict
   base[uint64_t(d) * kRadix + v] = block_exclusive_scan(h, s_scan);
 }
 
-__global__ void k_identity(const ReadIndex R, uint32_t n_reads, uint32_t* __restrict__ vals) {
+template <class V>
+__global__ void k_identity(const ReadIndex R, uint32_t n_reads, V* __restrict__ vals) {
   // One warp per read: vals[off_i + i + k] = (i << shift) | k, k = 0 .. L_i.
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t lane = threadIdx.x & 31;
   for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n_reads; i += warps) {
-    const Suffix s = decode(R, i << R.shift);
+    const Suffix s = decode(R, V(i) << R.shift);
     const uint64_t row0 = s.off + i;
-    for (uint32_t k = lane; k <= s.len; k += 32) vals[row0 + k] = (i << R.shift) | k;
+    for (uint32_t k = lane; k <= s.len; k += 32) vals[row0 + k] = (V(i) << R.shift) | V(k);
   }
+}
+
+// Suffixes per bucket (first `bucket_bits` bits of the A-padded first window,
+// i.e. the first bucket_bits/2 bases) over every suffix of every read: the
+// "size" array of Figure 2 step 1.  One thread per read walks its suffixes
+// in address order; CTAs own 16384-bucket slabs (grid.y) in shared memory.
+constexpr uint32_t kBucketSlab = 16384;
+
+__global__ void __launch_bounds__(512) k_bucket_hist(const ReadIndex R, uint32_t n_reads, uint32_t bucket_bits,
+                                                     unsigned long long* __restrict__ hist) {
+  extern __shared__ uint32_t sh[];  // kBucketSlab counters
+  const uint32_t slab0 = blockIdx.y * kBucketSlab;
+  for (uint32_t x = threadIdx.x; x < kBucketSlab; x += blockDim.x) sh[x] = 0;
+  __syncthreads();
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_reads; i += gridDim.x * blockDim.x) {
+    Suffix s = decode(R, uint64_t(i) << R.shift);
+    const uint32_t L = s.len;
+    for (uint32_t k = 0; k <= L; ++k) {
+      s.k = k;
+      const uint32_t b = window16(R, s, 0) >> (32 - bucket_bits);
+      if (b - slab0 < kBucketSlab) atomicAdd(&sh[b - slab0], 1u);
+    }
+  }
+  __syncthreads();
+  const uint32_t n_buckets = 1u << bucket_bits;
+  for (uint32_t x = threadIdx.x; x < kBucketSlab && slab0 + x < n_buckets; x += blockDim.x)
+    if (sh[x]) atomicAdd(&hist[slab0 + x], (unsigned long long)sh[x]);
+}
+
+// Digit counts of the suffixes of one HBM-bounded pass (bucket in [lo, hi)),
+// every read of one length L: row 0 = suffix length (the read-major start
+// order's length digit), rows 1..4 = the four 8-bit digits of the first
+// window (most significant first).  Figure 2 step 3(a)'s rescan of all
+// suffixes for the selected partitions.
+__global__ void __launch_bounds__(512) k_pass_hist(const ReadIndex R, uint32_t n_reads, uint32_t bucket_bits,
+                                                   uint32_t lo, uint32_t hi, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t sh[5 * kRadix];
+  for (uint32_t x = threadIdx.x; x < 5 * kRadix; x += blockDim.x) sh[x] = 0;
+  __syncthreads();
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_reads; i += gridDim.x * blockDim.x) {
+    Suffix s = decode(R, uint64_t(i) << R.shift);
+    const uint32_t L = s.len;
+    for (uint32_t k = 0; k <= L; ++k) {
+      s.k = k;
+      const uint32_t key = window16(R, s, 0);
+      if ((key >> (32 - bucket_bits)) - lo < hi - lo) {
+        atomicAdd(&sh[min(L - k, 255u)], 1u);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) atomicAdd(&sh[(1 + j) * kRadix + ((key >> (24 - 8 * j)) & 255u)], 1u);
+      }
+    }
+  }
+  __syncthreads();
+  for (uint32_t x = threadIdx.x; x < 5 * kRadix; x += blockDim.x)
+    if (sh[x]) atomicAdd(&hist[x], sh[x]);
+}
+
+__global__ void __launch_bounds__(kRadix) k_scan_rows(uint32_t* hist) {
+  __shared__ uint32_t s_scan[kRadix / 32];
+  const uint32_t row = blockIdx.x, v = threadIdx.x;
+  const uint32_t x = hist[row * kRadix + v];
+  hist[row * kRadix + v] = block_exclusive_scan(x, s_scan);
 }
 
 __global__ void k_lenstats(const uint32_t* __restrict__ lens, uint64_t n, unsigned long long* out) {
@@ -148,13 +211,39 @@ cudaError_t launch_digitbase(const uint32_t* P, uint32_t q_max, uint32_t D, int 
   return cudaGetLastError();
 }
 
-cudaError_t launch_identity(const ReadIndex& R, uint32_t n_reads, const uint64_t* /*unused*/, uint32_t* vals,
-                            cudaStream_t st) {
+cudaError_t launch_identity(const ReadIndex& R, uint32_t n_reads, void* vals, int id_bytes, cudaStream_t st) {
   if (n_reads == 0) return cudaSuccess;
   const uint32_t threads = 256;
   uint64_t blocks = (uint64_t(n_reads) * 32 + threads - 1) / threads;
   if (blocks > 65535u * 4u) blocks = 65535u * 4u;
-  k_identity<<<uint32_t(blocks), threads, 0, st>>>(R, n_reads, vals);
+  if (id_bytes == 8) k_identity<uint64_t><<<uint32_t(blocks), threads, 0, st>>>(R, n_reads, static_cast<uint64_t*>(vals));
+  else k_identity<uint32_t><<<uint32_t(blocks), threads, 0, st>>>(R, n_reads, static_cast<uint32_t*>(vals));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_hist(const ReadIndex& R, uint32_t n_reads, uint32_t bucket_bits, unsigned long long* hist,
+                               int sm_count, cudaStream_t st) {
+  const uint32_t slabs = ((1u << bucket_bits) + kBucketSlab - 1) / kBucketSlab;
+  uint32_t gx = (n_reads + 511) / 512;
+  const uint32_t cap = max(1u, uint32_t(2 * sm_count) / slabs);
+  if (gx > cap) gx = cap;
+  if (gx == 0) gx = 1;
+  const int smem = int(kBucketSlab * sizeof(uint32_t));
+  cudaError_t e = cudaFuncSetAttribute(k_bucket_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  k_bucket_hist<<<dim3(gx, slabs), 512, smem, st>>>(R, n_reads, bucket_bits, hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass_hist(const ReadIndex& R, uint32_t n_reads, uint32_t bucket_bits, uint32_t lo, uint32_t hi,
+                             uint32_t* hist, int sm_count, cudaStream_t st) {
+  uint32_t gx = (n_reads + 511) / 512;
+  if (gx > uint32_t(2 * sm_count)) gx = 2 * sm_count;
+  if (gx == 0) gx = 1;
+  k_pass_hist<<<gx, 512, 0, st>>>(R, n_reads, bucket_bits, lo, hi, hist);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_scan_rows<<<5, kRadix, 0, st>>>(hist);
   return cudaGetLastError();
 }
 

@@ -8,34 +8,42 @@ namespace cxbwt {
 
 // Where a digit pass takes its items from.
 enum SrcMode : int {
-  // Position j of the initial order is generated, not loaded: suffix length
-  // j / n, read j % n (every read of one length).  The key window is gathered.
+  // Item j of the (suffix length, read) start order is generated, not loaded:
+  // suffix length j / n, read j % n (every read of one length).  The key
+  // window is gathered.
   kSrcInitUniform = 0,
-  // Values are loaded; the key window is gathered from the store by value.
+  // Ids are loaded; the key window is gathered from the store by id.
   kSrcExtract = 1,
-  // Values and the key window carried from the previous pass are loaded.
+  // Ids and the key window carried from the previous pass are loaded.
   kSrcCarried = 2,
-  // Values are loaded; the key is the suffix length (the (length, read) start
-  // order of reads of different lengths).
+  // Ids are loaded; the digit is a byte of the suffix length (the (length,
+  // read) start order for reads of different lengths).
   kSrcLength = 3,
+  // Item j of the read-major order (read j / (L+1), offset j % (L+1)) is
+  // generated; the first window is gathered and carried; the digit is the
+  // suffix length (at most 255).  Gathers walk the store in address order.
+  kSrcInitReadMajor = 4,
 };
 
 struct PassArgs {
-  const uint32_t* vals_in;
+  const void* vals_in;               // suffix ids (uint32 or uint64)
   const uint32_t* keys_in;
-  uint32_t* vals_out;
+  void* vals_out;
   uint32_t* keys_out;                // nullptr when the next pass gathers a new window
   const uint32_t* digit_base;        // [256] first output row of each digit value
   unsigned long long* status;        // [n_tiles * 256] look-back words of this pass
   uint32_t* tile_counter;            // zero on entry; the kernel leaves it zero
   uint32_t* err;                     // device error word
   ReadIndex R;
-  uint32_t n_items;
+  uint64_t n_gen;                    // input rows (loaded or generated)
+  uint32_t n_out;                    // output rows (n_gen unless a bucket filter drops some)
   uint32_t n_tiles;
   uint32_t epoch;                    // look-back flags of this pass: 2*epoch, 2*epoch+1
   uint32_t key_shift;                // digit = (key >> key_shift) & 255
   uint32_t window_c0;                // gathered window: suffix bases [c0, c0 + 16)
-  uint32_t n_reads;                  // kSrcInitUniform
+  uint32_t n_reads;                  // generated modes
+  uint32_t bucket_shift;             // filter: keep rows with (key >> bucket_shift) in [bucket_lo, bucket_hi)
+  uint32_t bucket_lo, bucket_hi;
   uint64_t timeout_ns;               // look-back wait limit
 };
 
@@ -45,9 +53,13 @@ struct TileShape {
   int items_per_thread;
   int tile() const { return threads * items_per_thread; }
 };
-TileShape onesweep_shape(int tile_items_hint);
-size_t onesweep_smem_bytes(const TileShape& s);
-cudaError_t launch_onesweep(const PassArgs& a, int mode, bool write_key, const TileShape& shape, cudaStream_t st);
+TileShape onesweep_shape(int tile_items_hint, int id_bytes);
+// id_bytes: 4 or 8.  filter: drop rows outside the bucket range (generated modes only).
+cudaError_t launch_onesweep(const PassArgs& a, int mode, bool write_key, bool filter, int id_bytes,
+                            const TileShape& shape, cudaStream_t st);
+template <class V>
+cudaError_t launch_onesweep_t(const PassArgs& a, int mode, bool write_key, bool filter, const TileShape& shape,
+                              cudaStream_t st);
 
 // Per-position 4-mer counts P[q][v] (q < q_max) over all reads.
 cudaError_t launch_poscount(const ReadIndex& R, uint32_t n_reads, uint32_t q_max, uint32_t* P, int sm_count,
@@ -56,23 +68,35 @@ cudaError_t launch_poscount(const ReadIndex& R, uint32_t n_reads, uint32_t q_max
 // base[d][v].  lenhist (q_max+1 entries) is used when not uniform.
 cudaError_t launch_digitbase(const uint32_t* P, uint32_t q_max, uint32_t D, int uniform, uint32_t n_reads,
                              uint32_t uniform_len, const uint32_t* lenhist, uint32_t* base, cudaStream_t st);
-// vals[soff_i + k] = (i << shift) | k for every read i and k in [0, L_i].
-cudaError_t launch_identity(const ReadIndex& R, uint32_t n_reads, const uint64_t* soff, uint32_t* vals,
-                            cudaStream_t st);
+// vals[off_i + i + k] = (i << shift) | k for every read i and k in [0, L_i].
+cudaError_t launch_identity(const ReadIndex& R, uint32_t n_reads, void* vals, int id_bytes, cudaStream_t st);
+// Suffixes per bucket of the first bucket_bits / 2 bases (hist: 2^bucket_bits
+// zeroed uint64 counters).
+cudaError_t launch_bucket_hist(const ReadIndex& R, uint32_t n_reads, uint32_t bucket_bits, unsigned long long* hist,
+                               int sm_count, cudaStream_t st);
+// First output row of each digit value, for the suffixes with bucket in
+// [lo, hi): row 0 = suffix length, rows 1..4 = first-window digits
+// (hist: 5 x 256 zeroed counters, replaced by exclusive sums).
+cudaError_t launch_pass_hist(const ReadIndex& R, uint32_t n_reads, uint32_t bucket_bits, uint32_t lo, uint32_t hi,
+                             uint32_t* hist, int sm_count, cudaStream_t st);
 // min / max / sum of n lengths and the number of invalid ones (0 or > 65535):
 // out[0] = min, out[1] = max, out[2] = sum, out[3] = invalid (out zeroed by caller
 // except out[0] = UINT64_MAX).
 cudaError_t launch_lenstats(const uint32_t* lens, uint64_t n, unsigned long long* out, cudaStream_t st);
 
 struct EmitArgs {
-  const uint32_t* sa;        // sorted values
-  uint32_t n;                // N
+  const void* sa;            // sorted ids of this slice's rows (uint32 or uint64)
+  uint32_t n;                // rows in the slice
+  uint64_t row0;             // global BWT row of the slice's row 0
+  uint64_t n_total;          // rows of the whole BWT
   ReadIndex R;
-  uint32_t* bwt;             // ceil(N/16) words
-  uint64_t* dollar_pos;      // per read, may be null
-  unsigned long long* counts;// [5], zeroed by the caller
-  uint64_t* sa_out;          // (i << 16) | k per rank, may be null
+  uint32_t* bwt;             // global word w is bwt[w - word_base]
+  uint64_t word_base;
+  uint64_t* dollar_pos;      // per read (global rows), may be null
+  unsigned long long* counts;// [5], accumulated
+  uint64_t* sa_out;          // (i << 16) | k per slice row (sa_out[r]), may be null
   uint32_t* err;             // device error word
+  int id_bytes;              // 4 or 8
 };
 cudaError_t launch_emit(const EmitArgs& a, cudaStream_t st);
 

@@ -25,12 +25,15 @@
 //      that runs of equal digits go to consecutive addresses.
 // The only wait is in step 4.  It is bounded by a wall-clock limit; when the
 // limit passes the kernel records kErrTimeout and finishes (it never traps).
+#pragma once
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "kernels.cuh"
 
 namespace cxbwt {
-namespace {
+namespace onesweep {
 
 template <int THREADS>
 __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t x, uint32_t* scratch /*[8]*/) {
@@ -53,22 +56,28 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t x, uint32_
   return warp_prefix + incl - x;
 }
 
-template <int THREADS, int IPT, int MIN_BLOCKS, int MODE, bool WRITE_KEY>
+template <class V, int THREADS, int IPT, int MIN_BLOCKS, int MODE, bool WRITE_KEY, bool FILTER>
 __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs a) {
   constexpr int TILE = THREADS * IPT;
   constexpr int WARPS = THREADS / 32;
+  constexpr bool GEN = (MODE == kSrcInitUniform || MODE == kSrcInitReadMajor);
+  constexpr bool LEN_DIGIT = (MODE == kSrcInitReadMajor);  // digit = suffix length, key = window 0
+  using I = typename std::conditional<GEN, uint64_t, uint32_t>::type;  // generated inputs may exceed 2^32 rows
   static_assert(THREADS >= 256 && THREADS % 32 == 0, "one thread per digit value is needed");
+  static_assert(!FILTER || GEN, "the bucket filter applies to generated inputs");
 
-  extern __shared__ __align__(16) uint32_t s_stage[];  // keys [TILE], then values [TILE]
+  extern __shared__ __align__(16) uint32_t s_stage[];  // keys [TILE], then ids [TILE]
   uint32_t* s_keys = s_stage;
-  uint32_t* s_vals = s_stage + TILE;
+  V* s_vals = reinterpret_cast<V*>(s_stage + TILE);
   // Per-warp digit counts; after the look-back, the tile-local row of the
   // warp's first item of each digit.
   __shared__ uint32_t s_whist[WARPS][kRadix];
   __shared__ uint32_t s_gbase[kRadix];  // global row of tile-local row 0 of each digit
   __shared__ uint32_t s_scan[8];
-  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_tile, s_kept;
 
+  const V* vals_in = static_cast<const V*>(a.vals_in);
+  V* vals_out = static_cast<V*>(a.vals_out);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < WARPS * kRadix; i += THREADS) (&s_whist[0][0])[i] = 0u;
   if (tid == 0) {
@@ -79,35 +88,45 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
   }
   __syncthreads();
   const uint32_t tile = s_tile;
-  const uint32_t tile_base = tile * uint32_t(TILE);  // n_items < 2^32
-  const uint32_t warp_base = tile_base + uint32_t(warp) * 32u * IPT + lane;
-  const uint32_t n_items = a.n_items;
+  const I tile_base = I(tile) * I(TILE);
+  const I warp_base = tile_base + I(warp) * 32u * IPT + lane;
+  const I n_in = I(a.n_gen);
 
-  uint32_t key[IPT], val[IPT], digit[IPT];
+  uint32_t key[IPT], digit[IPT];
+  V val[IPT];
 
   // ---- 2. load ------------------------------------------------------------
   if (MODE == kSrcInitUniform) {
     const uint32_t L = a.R.uniform_len;
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
-      const uint32_t idx = warp_base + j * 32;
-      // Position idx of the (suffix length, read) order: length idx / n, read idx % n.
-      const uint32_t slen = idx / a.n_reads;
-      const uint32_t i = idx - slen * a.n_reads;
-      val[j] = (i << a.R.shift) | (L - min(slen, L));
+      const I idx = warp_base + j * 32;
+      // Row idx of the (suffix length, read) order: length idx / n, read idx % n.
+      const I slen = idx / a.n_reads;
+      const uint32_t i = uint32_t(idx - slen * a.n_reads);
+      val[j] = (V(i) << a.R.shift) | V(L - uint32_t(min(slen, I(L))));
+    }
+  } else if (MODE == kSrcInitReadMajor) {
+    const uint32_t L1 = a.R.uniform_len + 1;
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const I idx = warp_base + j * 32;
+      // Row idx of the read-major order: read idx / (L+1), offset idx % (L+1).
+      const I i = idx / L1;
+      val[j] = (V(i) << a.R.shift) | V(uint32_t(idx - i * L1));
     }
   } else {
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
-      const uint32_t idx = warp_base + j * 32;
-      val[j] = idx < n_items ? __ldg(a.vals_in + idx) : 0u;
+      const I idx = warp_base + j * 32;
+      val[j] = idx < n_in ? vals_in[idx] : V(0);
     }
   }
   if (MODE == kSrcCarried) {
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
-      const uint32_t idx = warp_base + j * 32;
-      key[j] = idx < n_items ? __ldg(a.keys_in + idx) : 0u;
+      const I idx = warp_base + j * 32;
+      key[j] = idx < n_in ? __ldg(a.keys_in + idx) : 0u;
     }
   } else if (MODE == kSrcLength) {
 #pragma unroll
@@ -118,24 +137,30 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
   } else {
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
-      const uint32_t idx = warp_base + j * 32;
-      key[j] = idx < n_items ? window16(a.R, decode(a.R, val[j]), a.window_c0) : 0u;
+      const I idx = warp_base + j * 32;
+      key[j] = idx < n_in ? window16(a.R, decode(a.R, val[j]), a.window_c0) : 0u;
     }
   }
 #pragma unroll
   for (int j = 0; j < IPT; ++j) {
-    const uint32_t idx = warp_base + j * 32;
-    // Items past the end get a value no digit has, so they match only each other.
-    digit[j] = idx < n_items ? ((key[j] >> a.key_shift) & (kRadix - 1)) : uint32_t(kRadix);
+    const I idx = warp_base + j * 32;
+    bool keep = idx < n_in;
+    if (FILTER) keep = keep && ((key[j] >> a.bucket_shift) - a.bucket_lo) < (a.bucket_hi - a.bucket_lo);
+    uint32_t d;
+    if (LEN_DIGIT) d = a.R.uniform_len - (uint32_t(val[j]) & ((1u << a.R.shift) - 1u));
+    else d = (key[j] >> a.key_shift) & (kRadix - 1);
+    // Rows past the end (or filtered out) get a value no digit has, so they
+    // match only each other and are neither counted nor written.
+    digit[j] = keep ? d : uint32_t(kRadix);
   }
 
   // ---- 3. stable rank inside the warp, in item order ------------------------
   // Lanes holding the same digit are found with one ballot per digit bit (a
-  // 9th bit separates the items past the end, only in the last tile): cheaper
-  // on sm_103a than __match_any_sync.  digit[j] becomes
+  // 9th bit separates dropped rows: only in the last tile unless filtering):
+  // cheaper on sm_103a than __match_any_sync.  digit[j] becomes
   // (rank of the item among the warp's items of its digit) << 9 | digit.
   const uint32_t lt = lanemask_lt();
-  const bool tail_tile = (tile == a.n_tiles - 1);
+  const bool ninth = FILTER || (tile == a.n_tiles - 1);
 #pragma unroll
   for (int j = 0; j < IPT; ++j) {
     const uint32_t d = digit[j];
@@ -146,7 +171,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
       const uint32_t m = __ballot_sync(0xFFFFFFFFu, bit);
       peers &= bit ? m : ~m;
     }
-    if (tail_tile) {
+    if (ninth) {
       const uint32_t bit = d >> kRadixBits;
       const uint32_t m = __ballot_sync(0xFFFFFFFFu, bit);
       peers &= bit ? m : ~m;
@@ -179,6 +204,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
     store_relaxed_u64(a.status + uint64_t(tile) * kRadix + tid, (tile == 0 ? pre_flag : agg_flag) | tile_cnt);
   }
   const uint32_t local_excl = block_exclusive_scan_256<THREADS>(tile_cnt, s_scan);
+  if (tid == kRadix - 1) s_kept = local_excl + tile_cnt;  // rows of this tile that are written
   if (tid < kRadix) {
 #pragma unroll
     for (int w = 0; w < WARPS; ++w) s_whist[w][tid] += local_excl;
@@ -227,17 +253,19 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
     }
   }
   __syncthreads();
-  const uint32_t left = n_items - tile_base;
-  const uint32_t n_valid = left < uint32_t(TILE) ? left : uint32_t(TILE);
+  const uint32_t n_valid = s_kept;
 #pragma unroll
   for (int j = 0; j < IPT; ++j) {
     const uint32_t r = j * THREADS + tid;
     if (r < n_valid) {
       const uint32_t k = s_keys[r];
-      const uint32_t d = (k >> a.key_shift) & (kRadix - 1);
+      const V v = s_vals[r];
+      uint32_t d;
+      if (LEN_DIGIT) d = a.R.uniform_len - (uint32_t(v) & ((1u << a.R.shift) - 1u));
+      else d = (k >> a.key_shift) & (kRadix - 1);
       const uint32_t g = s_gbase[d] + r;
-      if (g < n_items) {
-        a.vals_out[g] = s_vals[r];
+      if (g < a.n_out) {
+        vals_out[g] = v;
         if (WRITE_KEY) a.keys_out[g] = k;
       } else {
         atomicOr(a.err, kErrBounds);  // digit bases disagree with the items: never write out of bounds
@@ -252,11 +280,13 @@ template <int T, int I, int B>
 struct Shape {
   static constexpr int threads = T, ipt = I, min_blocks = B;
 };
+using ShapeMid = Shape<256, 16, 4>;    // 4096 items
+using ShapeLarge = Shape<512, 16, 2>;  // 8192 items
 
-template <class S, int MODE, bool WK>
+template <class V, class S, int MODE, bool WK, bool F>
 cudaError_t launch_mode(const PassArgs& a, cudaStream_t st) {
-  const size_t smem = size_t(S::threads) * S::ipt * 2 * sizeof(uint32_t);
-  auto kern = k_onesweep<S::threads, S::ipt, S::min_blocks, MODE, WK>;
+  const size_t smem = size_t(S::threads) * S::ipt * (sizeof(uint32_t) + sizeof(V));
+  auto kern = k_onesweep<V, S::threads, S::ipt, S::min_blocks, MODE, WK, F>;
   static bool configured = false;  // per instantiation; attributes are per function
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -269,42 +299,30 @@ cudaError_t launch_mode(const PassArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <class S>
-cudaError_t launch_shape(const PassArgs& a, int mode, bool write_key, cudaStream_t st) {
+template <class V, class S>
+cudaError_t launch_shape(const PassArgs& a, int mode, bool wk, bool filter, cudaStream_t st) {
   switch (mode) {
-    case kSrcInitUniform: return write_key ? launch_mode<S, kSrcInitUniform, true>(a, st)
-                                           : launch_mode<S, kSrcInitUniform, false>(a, st);
-    case kSrcExtract: return write_key ? launch_mode<S, kSrcExtract, true>(a, st)
-                                       : launch_mode<S, kSrcExtract, false>(a, st);
-    case kSrcCarried: return write_key ? launch_mode<S, kSrcCarried, true>(a, st)
-                                       : launch_mode<S, kSrcCarried, false>(a, st);
-    case kSrcLength: return write_key ? launch_mode<S, kSrcLength, true>(a, st)
-                                      : launch_mode<S, kSrcLength, false>(a, st);
+    case kSrcInitUniform:
+      if (filter) return wk ? launch_mode<V, S, kSrcInitUniform, true, true>(a, st)
+                            : launch_mode<V, S, kSrcInitUniform, false, true>(a, st);
+      return wk ? launch_mode<V, S, kSrcInitUniform, true, false>(a, st)
+                : launch_mode<V, S, kSrcInitUniform, false, false>(a, st);
+    case kSrcInitReadMajor:
+      if (!wk) return cudaErrorInvalidValue;  // it exists to carry window 0
+      return filter ? launch_mode<V, S, kSrcInitReadMajor, true, true>(a, st)
+                    : launch_mode<V, S, kSrcInitReadMajor, true, false>(a, st);
+    case kSrcExtract:
+      if (filter) return cudaErrorInvalidValue;
+      return wk ? launch_mode<V, S, kSrcExtract, true, false>(a, st) : launch_mode<V, S, kSrcExtract, false, false>(a, st);
+    case kSrcCarried:
+      if (filter) return cudaErrorInvalidValue;
+      return wk ? launch_mode<V, S, kSrcCarried, true, false>(a, st) : launch_mode<V, S, kSrcCarried, false, false>(a, st);
+    case kSrcLength:
+      if (filter || wk) return cudaErrorInvalidValue;
+      return launch_mode<V, S, kSrcLength, false, false>(a, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
-using ShapeSmall = Shape<256, 8, 6>;    // 2048 items
-using ShapeMid = Shape<256, 16, 4>;     // 4096 items
-using ShapeLarge = Shape<512, 16, 2>;   // 8192 items
-
-}  // namespace
-
-TileShape onesweep_shape(int tile_items_hint) {
-  if (tile_items_hint == 2048) return TileShape{ShapeSmall::threads, ShapeSmall::ipt};
-  if (tile_items_hint == 8192) return TileShape{ShapeLarge::threads, ShapeLarge::ipt};
-  return TileShape{ShapeMid::threads, ShapeMid::ipt};
-}
-
-size_t onesweep_smem_bytes(const TileShape& s) { return size_t(s.tile()) * 2 * sizeof(uint32_t); }
-
-cudaError_t launch_onesweep(const PassArgs& a, int mode, bool write_key, const TileShape& s, cudaStream_t st) {
-  if (a.n_tiles == 0) return cudaSuccess;
-  if (s.threads == ShapeSmall::threads && s.items_per_thread == ShapeSmall::ipt)
-    return launch_shape<ShapeSmall>(a, mode, write_key, st);
-  if (s.threads == ShapeLarge::threads && s.items_per_thread == ShapeLarge::ipt)
-    return launch_shape<ShapeLarge>(a, mode, write_key, st);
-  return launch_shape<ShapeMid>(a, mode, write_key, st);
-}
-
+}  // namespace onesweep
 }  // namespace cxbwt

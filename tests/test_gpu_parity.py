@@ -135,7 +135,7 @@ def test_budget_too_small_is_enomem():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     codes, lens = synth.uniform_reads(10_000, 100, 1)
-    with binding.Context(device=0, budget_bytes=8 << 20) as c:
+    with binding.Context(device=0, budget_bytes=1 << 20) as c:
         with pytest.raises(binding.CxbwtError) as e:
             c.build(binding.pack_codes(codes), lens)
         assert e.value.status == -2
