@@ -18,9 +18,12 @@ def _need_gpu():
         pytest.skip("no CUDA device")
 
 
-def budget_for(n_suffixes, slices, id_bytes=4):
-    """A budget that leaves room for about n_suffixes / slices rows per slice."""
-    per_row = 2 * id_bytes + 8 + 8 * 256 / 4096 + 8 / 33 + 1
+def budget_for(n_suffixes, slices, id_bytes=4, host_sa=False):
+    """A budget that leaves room for about n_suffixes / slices rows per slice
+    (one slice: twice what it needs)."""
+    per_row = 2 * id_bytes + 8 + 8 * 256 / 4096 + 8 / 33 + 1 + (8 if host_sa else 0)
+    if slices == 1:
+        return int(6 << 20) + int(2 * per_row * n_suffixes)
     return int(6 << 20) + int(per_row * n_suffixes / slices)
 
 
@@ -39,7 +42,7 @@ def test_slices_identical(genome_reads, slices, flags, where):
     from paper_1401_7457_gb300 import binding
     codes, lens, ref = genome_reads
     N = int(lens.sum()) + lens.size
-    with binding.Context(device=0, budget_bytes=budget_for(N, slices, 8 if flags & 1 else 4),
+    with binding.Context(device=0, budget_bytes=budget_for(N, slices, 8 if flags & 1 else 4, where == "host"),
                          plan_flags=flags) as c:
         got = gpu_bwt(c, codes, lens, where=where, want_sa=True)
         st = c.stats()
