@@ -98,22 +98,41 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
   // ---- 2. load ------------------------------------------------------------
   if (MODE == kSrcInitUniform) {
     const uint32_t L = a.R.uniform_len;
+    if (a.n_gen <= 0xFFFFFFFFull) {  // 32-bit division while the enumeration fits
 #pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-      const I idx = warp_base + j * 32;
-      // Row idx of the (suffix length, read) order: length idx / n, read idx % n.
-      const I slen = idx / a.n_reads;
-      const uint32_t i = uint32_t(idx - slen * a.n_reads);
-      val[j] = (V(i) << a.R.shift) | V(L - uint32_t(min(slen, I(L))));
+      for (int j = 0; j < IPT; ++j) {
+        const uint32_t idx = uint32_t(warp_base) + j * 32;
+        // Row idx of the (suffix length, read) order: length idx / n, read idx % n.
+        const uint32_t slen = idx / a.n_reads;
+        const uint32_t i = idx - slen * a.n_reads;
+        val[j] = (V(i) << a.R.shift) | V(L - min(slen, L));
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        const I idx = warp_base + j * 32;
+        const I slen = idx / a.n_reads;
+        const uint32_t i = uint32_t(idx - slen * a.n_reads);
+        val[j] = (V(i) << a.R.shift) | V(L - uint32_t(min(slen, I(L))));
+      }
     }
   } else if (MODE == kSrcInitReadMajor) {
     const uint32_t L1 = a.R.uniform_len + 1;
+    if (a.n_gen <= 0xFFFFFFFFull) {
 #pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-      const I idx = warp_base + j * 32;
-      // Row idx of the read-major order: read idx / (L+1), offset idx % (L+1).
-      const I i = idx / L1;
-      val[j] = (V(i) << a.R.shift) | V(uint32_t(idx - i * L1));
+      for (int j = 0; j < IPT; ++j) {
+        const uint32_t idx = uint32_t(warp_base) + j * 32;
+        // Row idx of the read-major order: read idx / (L+1), offset idx % (L+1).
+        const uint32_t i = idx / L1;
+        val[j] = (V(i) << a.R.shift) | V(idx - i * L1);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        const I idx = warp_base + j * 32;
+        const I i = idx / L1;
+        val[j] = (V(i) << a.R.shift) | V(uint32_t(idx - i * L1));
+      }
     }
   } else {
 #pragma unroll
