@@ -40,6 +40,27 @@ METRIC = "BWT build Gbases/s at 1 GB300 (% HBM roofline); served p50/p99 vs plai
 UNIT = "Gbase/s"
 WORKLOAD = ("genome-like: {n:,} reads x 100 bp from both strands of a seeded 5 Mbp uniform genome "
             "(1M reads = 20x coverage), 1% substitutions, seed 2; {N:,} suffixes")
+WORKLOADS = {
+    "genome-like": WORKLOAD,
+    "repeat-rich": ("repeat-rich: {n:,} reads x 100 bp from a seeded 100 Mbp genome, 5% in 10-copy 1 kb repeats "
+                    "at 0.5% divergence, both strands, 1% substitutions, seed 3; {N:,} suffixes"),
+    "tiny": "tiny: {n:,} reads x 100 bp, i.i.d. uniform bases, seed 1; {N:,} suffixes",
+}
+
+
+def load_workload(name, rank=0, n_reads=0):
+    """(description, codes, lens) of a workload; rank > 0 draws an independent collection of the same shape."""
+    from paper_1401_7457_gb300 import synth
+    if name == "genome-like":
+        seed = 2 if rank == 0 else synth.derive_seed(2, rank)
+        codes, lens = synth.genome_like(seed=seed, n_reads=n_reads or 1_000_000)
+    elif name == "repeat-rich":
+        seed = 3 if rank == 0 else synth.derive_seed(3, rank)
+        codes, lens = synth.repeat_rich(seed=seed, n_reads=n_reads or 50_000_000)
+    else:
+        seed = 1 if rank == 0 else synth.derive_seed(1, rank)
+        codes, lens = synth.uniform_reads(n_reads or 10_000, 100, seed)
+    return WORKLOADS[name], codes, lens
 SORT_BYTES_PER_ITEM = 16  # algorithmic bytes per suffix per digit pass: 4 B key + 4 B id, read and written
 PROFILE = os.path.join(ROOT, "profiles", "onesweep_digit_pass_genome_like.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_1401_7457_gb300", "csrc", "k_sort.cu")
@@ -149,9 +170,8 @@ def run_reference(args, rank, world):
     if rank != 0:
         return 0
     import oracle
-    from paper_1401_7457_gb300 import synth
     oracle.build()
-    codes, lens = synth.genome_like()
+    desc, codes, lens = load_workload(args.workload, 0, args.reads)
     threads = os.cpu_count() or 1
     n_sample = args.cpu_sample_reads
     for _ in range(args.warmup):
@@ -167,7 +187,7 @@ def run_reference(args, rank, world):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-            "data": "synthetic", "config": {"workload": WORKLOAD.format(n=lens.size, N=int(lens.sum()) + lens.size)},
+            "data": "synthetic", "config": {"workload": desc.format(n=lens.size, N=int(lens.sum()) + lens.size)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -182,8 +202,12 @@ def main():
     ap.add_argument("--impl", default="cxbwt", choices=["cxbwt", "reference"])
     ap.add_argument("--cpu-sample-reads", type=int, default=500_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--reads", type=int, default=1_000_000,
-                    help="reads per GPU (default: the 1M-read workload; smaller only for profiling captures)")
+    ap.add_argument("--reads", type=int, default=0,
+                    help="reads per GPU (0: the workload's own size; smaller only for profiling captures)")
+    ap.add_argument("--workload", default="genome-like", choices=sorted(WORKLOADS),
+                    help="genome-like is the benchmark; the others are parity-test workloads timed for reference")
+    ap.add_argument("--budget-gb", type=float, default=0.0,
+                    help="device budget of the library context (0: 90%% of free memory)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -201,8 +225,7 @@ def main():
     build.build()
 
     # Each rank builds its own independent collection (weak scaling, no data-path collective).
-    seed = 2 if rank == 0 else synth.derive_seed(2, rank)
-    codes, lens = synth.genome_like(seed=seed, n_reads=args.reads)
+    desc, codes, lens = load_workload(args.workload, rank, args.reads)
     words = binding.pack_codes(codes)
     n = lens.size
     bases = int(lens.sum())
@@ -217,7 +240,7 @@ def main():
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    ctx = binding.Context(device=local, timing=True)
+    ctx = binding.Context(device=local, timing=True, budget_bytes=int(args.budget_gb * (1 << 30)))
 
     def step():
         ctx.build(d_words, d_lens, d_bwt, d_dpos, d_cnt, stream=stream)
@@ -268,7 +291,7 @@ def main():
     h_bwt = torch.empty(n_words, dtype=torch.int32).pin_memory()
     h_dpos = torch.empty(n, dtype=torch.int64).pin_memory()
     h_cnt = torch.zeros(5, dtype=torch.int64).pin_memory()
-    ctx2 = binding.Context(device=local)
+    ctx2 = binding.Context(device=local, budget_bytes=int(args.budget_gb * (1 << 30)))
     for _ in range(2):
         ctx2.build(h_words, h_lens, h_bwt, h_dpos, h_cnt, stream=stream)
     ctx2.reset_stats()
@@ -306,13 +329,14 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-                "config": {"workload": WORKLOAD.format(n=n, N=N), "n_reads": n, "read_len": int(lens[0]), "bases_per_gpu": bases,
+                "config": {"workload": desc.format(n=n, N=N), "n_reads": n, "read_len": int(lens[0]), "bases_per_gpu": bases,
                            "suffixes_per_gpu": N, "l2": "flushed between steps (512 MB write outside the events)",
                            "input": "device-resident (HBM) before the timed region; outputs left in HBM"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(st["kernel_launches"]), "gpu_launches_per_step": launches_per_step,
                 "clocks": clocks.summary(),
-                "detail": {"step_ms": ms, "sort_pass_ms_per_step": st["sort_pass_ms"] / args.steps,
+                "detail": {"step_ms": ms, "slices_per_step": st["slices"] / args.steps,
+                           "sort_pass_ms_per_step": st["sort_pass_ms"] / args.steps,
                            "group_finish_ms_per_step": st["group_ms"] / args.steps,
                            "emit_ms_per_step": st["emit_ms"] / args.steps,
                            "build_ms_per_step_lib": st["build_ms"] / args.steps}}
