@@ -556,9 +556,12 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   // ---- slices --------------------------------------------------------------
   // Device bytes per suffix of a slice: ids and keys (double-buffered),
   // look-back words, group lists; plus the SA staging when it goes to the host.
-  const double per_row = 2.0 * pl.idb + 8.0 + 8.0 * kRadix / TILE + 8.0 / 33 + (out_sa && !sa_dev ? 8.0 : 0.0);
+  // The look-back words cover every tile of a generated enumeration of all N
+  // suffixes, so they are a fixed cost, not a per-row one.
+  const double per_row = 2.0 * pl.idb + 8.0 + 8.0 / 33 + (out_sa && !sa_dev ? 8.0 : 0.0);
+  const uint64_t status_bytes = (pl.N + TILE - 1) / TILE * kRadix * 8;
   const uint64_t fixed = uint64_t(pl.Lmax) * kRadix * 4 + uint64_t(pl.D + pl.len_passes + 5) * kRadix * 4 +
-                         uint64_t(pl.W) * 4 * kRadix * 4 + (uint64_t(1) << kBucketBits) * 8 + (1u << 20);
+                         uint64_t(pl.W) * 4 * kRadix * 4 + (uint64_t(1) << kBucketBits) * 8 + status_bytes + (1u << 20);
   // Buffers sized per slice are reused (or regrown) by this build: they do
   // not count against what it may take.
   const uint64_t reusable = c->vals[0].cap + c->vals[1].cap + c->keys[0].cap + c->keys[1].cap + c->status.cap +

@@ -56,7 +56,7 @@ def test_repeat_rich_tenth_full_parity():
     from paper_1401_7457_gb300 import binding
     codes, lens = synth.repeat_rich(n_reads=5_000_000, genome_size=10_000_000)
     N = int(lens.sum()) + lens.size
-    budget = (2 << 30) + int(17.75 * N / 3)  # about a third of the suffixes per slice
+    budget = (2 << 30) + int(0.5 * N) + int(17.25 * N / 3)  # look-back words + a third of the suffixes per slice
     bwt, dpos, cnt, _, st = build_sliced(codes, lens, budget)
     assert st["slices"] >= 3, st
     ref = oracle.bwt(oracle.Collection(codes, lens), threads=THREADS)
@@ -70,7 +70,7 @@ def test_repeat_rich_full_size_sampled():
     n = lens.size
     N = int(lens.sum()) + n
     assert N == 5_050_000_000
-    budget = (2 << 30) + int(24.75 * N / 3)
+    budget = (2 << 30) + int(0.5 * N) + int(25.25 * N / 3)
     bwt, dpos, cnt, d_sa, st = build_sliced(codes, lens, budget, want_sa_device=True)
     assert st["slices"] >= 3, st
     # Exact counts: the input composition plus n terminators.

@@ -21,7 +21,7 @@ def _need_gpu():
 def budget_for(n_suffixes, slices, id_bytes=4, host_sa=False):
     """A budget that leaves room for about n_suffixes / slices rows per slice
     (one slice: twice what it needs)."""
-    per_row = 2 * id_bytes + 8 + 8 * 256 / 4096 + 8 / 33 + 1 + (8 if host_sa else 0)
+    per_row = 2 * id_bytes + 8 + 8 / 33 + 1 + (8 if host_sa else 0) + 0.5  # + look-back words
     if slices == 1:
         return int(6 << 20) + int(2 * per_row * n_suffixes)
     return int(6 << 20) + int(per_row * n_suffixes / slices)
