@@ -56,7 +56,7 @@ def test_repeat_rich_tenth_full_parity():
     from paper_1401_7457_gb300 import binding
     codes, lens = synth.repeat_rich(n_reads=5_000_000, genome_size=10_000_000)
     N = int(lens.sum()) + lens.size
-    budget = (2 << 30) + int(0.5 * N) + int(17.25 * N / 3)  # look-back words + a third of the suffixes per slice
+    budget = (400 << 20) + int(0.5 * N) + int(17.25 * N / 3)  # look-back words + a third of the suffixes per slice
     bwt, dpos, cnt, _, st = build_sliced(codes, lens, budget)
     assert st["slices"] >= 3, st
     ref = oracle.bwt(oracle.Collection(codes, lens), threads=THREADS)
