@@ -273,16 +273,19 @@ def main():
     value = bases * world * args.steps / (total_ms * 1e-3) / 1e9
 
     # Dominant kernel: the onesweep digit pass.
-    pass_ms = st["sort_pass_ms"] / max(st["sort_pass_launches"], 1)
-    achieved = SORT_BYTES_PER_ITEM * N / (pass_ms * 1e-3) / 1e9
+    launches = max(st["sort_pass_launches"], 1)
+    pass_ms = st["sort_pass_ms"] / launches
+    items_per_launch = st["sort_pass_items"] / launches  # N per launch for a one-slice build
+    achieved = SORT_BYTES_PER_ITEM * items_per_launch / (pass_ms * 1e-3) / 1e9 if pass_ms > 0 else 0.0
     peak, peak_kind = peak_hbm()
     traffic_per_item = profiled_traffic()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None if traffic_per_item is None else traffic_per_item * N,
+                "traffic": None if traffic_per_item is None else traffic_per_item * items_per_launch,
                 "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s",
                 "kernel": "k_onesweep (LSD digit pass)", "launches_per_step": st["sort_pass_launches"] / args.steps,
-                "algorithmic_bytes_per_launch": SORT_BYTES_PER_ITEM * N, "frac_of_nominal_8tbs": achieved / 8000.0}
+                "algorithmic_bytes_per_launch": SORT_BYTES_PER_ITEM * items_per_launch,
+                "avg_launch_ms": pass_ms, "frac_of_nominal_8tbs": achieved / 8000.0}
     launches_per_step = st["kernel_launches"] / args.steps
 
     # End to end through the C ABI with pinned host buffers (copies inside the timed region).

@@ -64,6 +64,7 @@ struct cxbwt_ctx {
   uint32_t epoch = 0;
   cudaStream_t side = nullptr;            // device -> host streaming of finished slices
   cudaEvent_t slice_done[2] = {nullptr, nullptr};
+  std::vector<cudaEvent_t> tev;           // timing events, 4 per slice (timing option)
   unsigned long long* h_small = nullptr;  // pinned: device error word, length stats
   cudaStream_t last_stream = nullptr;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -215,8 +216,10 @@ int take_device_error(cxbwt_ctx* c) {
 
 void* vptr(void* base, int idb, uint64_t row) { return static_cast<char*>(base) + row * uint64_t(idb); }
 
-// Sort the slice's suffixes into r.vals[cur]; returns cur (0 or 1) through *cur_out.
-int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out) {
+// Sort the slice's suffixes into r.vals[cur]; returns cur (0 or 1) through
+// *cur_out.  tev (or nullptr): events recorded before the digit passes and
+// after them.
+int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t* tev) {
   const Plan& pl = r.pl;
   cudaStream_t st = r.st;
   const uint32_t TILE = uint32_t(r.shape.tile());
@@ -251,6 +254,7 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out) {
     return r.base + size_t(1 + d) * kRadix;  // d in 0..3
   };
 
+  if (tev) CX_CUDA(c, cudaEventRecord(tev[0], st));
   int cur = 0, kin = 0;
   const int idb = pl.idb;
   bool first = pl.uniform;  // the first digit pass generates the start order
@@ -325,7 +329,7 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out) {
       r.sort_items += sl.rows;
     }
   }
-  if (c->opt.timing && sl.row0 == 0) CX_CUDA(c, cudaEventRecord(c->ev[2], st));
+  if (tev) CX_CUDA(c, cudaEventRecord(tev[1], st));
 
   // ---- group plan: finish every group of equal first windows on chip ---------
   if (pl.groups && pl.Lmax > 16) {
@@ -669,15 +673,22 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   CX_CUDA(c, cudaMemsetAsync(r.d_counts, 0, 5 * 8, st));
 
   const bool timing = c->opt.timing != 0;
-  if (timing) CX_CUDA(c, cudaEventRecord(c->ev[0], st));
-  if (timing) CX_CUDA(c, cudaEventRecord(c->ev[1], st));
+  if (timing) {
+    while (c->tev.size() < 4 * slices.size()) {
+      cudaEvent_t ev;
+      CX_CUDA(c, cudaEventCreate(&ev));
+      c->tev.push_back(ev);
+    }
+    CX_CUDA(c, cudaEventRecord(c->ev[0], st));
+  }
 
   uint64_t words_sent = 0;  // BWT words already streamed to the host
   for (size_t si = 0; si < slices.size(); ++si) {
     const Slice& sl = slices[si];
     int cur = 0;
-    CX_TRY(sort_slice(c, r, sl, &cur));
-    if (timing && si + 1 == slices.size()) CX_CUDA(c, cudaEventRecord(c->ev[4], st));
+    cudaEvent_t* tev = timing ? &c->tev[4 * si] : nullptr;
+    CX_TRY(sort_slice(c, r, sl, &cur, tev));
+    if (tev) CX_CUDA(c, cudaEventRecord(tev[2], st));
     // ---- emission of the slice -------------------------------------------
     EmitArgs e{};
     e.sa = r.vals[cur];
@@ -694,6 +705,7 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
     e.id_bytes = pl.idb;
     CX_CUDA(c, launch_emit(e, st));
     ++r.launches;
+    if (tev) CX_CUDA(c, cudaEventRecord(tev[3], st));
     if (out_sa && !sa_dev) {
       CX_CUDA(c, cudaMemcpyAsync(out_sa + sl.row0, r.d_sa, uint64_t(sl.rows) * 8, cudaMemcpyDeviceToHost, st));
       r.d2h += uint64_t(sl.rows) * 8;
@@ -748,16 +760,18 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   CX_CUDA(c, cudaStreamSynchronize(st));
   CX_TRY(take_device_error(c));
   if (timing) {
-    float ms_sort = 0, ms_all = 0, ms_group = 0, ms_emit = 0;
+    float ms_all = 0;
     CX_CUDA(c, cudaEventElapsedTime(&ms_all, c->ev[0], c->ev[3]));
-    if (slices.size() == 1) {
-      CX_CUDA(c, cudaEventElapsedTime(&ms_sort, c->ev[1], c->ev[2]));
-      CX_CUDA(c, cudaEventElapsedTime(&ms_group, c->ev[2], c->ev[4]));
-      CX_CUDA(c, cudaEventElapsedTime(&ms_emit, c->ev[4], c->ev[3]));
+    for (size_t si = 0; si < slices.size(); ++si) {
+      cudaEvent_t* tev = &c->tev[4 * si];
+      float ms_sort = 0, ms_group = 0, ms_emit = 0;
+      CX_CUDA(c, cudaEventElapsedTime(&ms_sort, tev[0], tev[1]));
+      CX_CUDA(c, cudaEventElapsedTime(&ms_group, tev[1], tev[2]));
+      CX_CUDA(c, cudaEventElapsedTime(&ms_emit, tev[2], tev[3]));
+      c->stats.sort_pass_ms += ms_sort;
+      c->stats.group_ms += ms_group;
+      c->stats.emit_ms += ms_emit;
     }
-    c->stats.sort_pass_ms += ms_sort;
-    c->stats.group_ms += ms_group;
-    c->stats.emit_ms += ms_emit;
     c->stats.build_ms += ms_all;
   }
   c->stats.builds += 1;
@@ -844,6 +858,7 @@ void cxbwt_destroy(cxbwt_ctx* c) {
     if (ev) cudaEventDestroy(ev);
   for (auto& ev : c->slice_done)
     if (ev) cudaEventDestroy(ev);
+  for (auto& ev : c->tev) cudaEventDestroy(ev);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->h_small) cudaFreeHost(c->h_small);
   delete c;

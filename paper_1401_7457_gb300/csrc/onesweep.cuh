@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
       const I idx = warp_base + j * 32;
-      val[j] = idx < n_in ? vals_in[idx] : V(0);
+      val[j] = idx < n_in ? __ldg(vals_in + idx) : V(0);
     }
   }
   if (MODE == kSrcCarried) {
