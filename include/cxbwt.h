@@ -185,6 +185,46 @@ int cxbwt_sync(cxbwt_ctx* ctx);
 int cxbwt_get_stats(const cxbwt_ctx* ctx, cxbwt_stats* out);
 int cxbwt_reset_stats(cxbwt_ctx* ctx);
 
+/* ---- a build that allocates nothing ---------------------------------------
+ *
+ * The paper has no counterpart to this call; it serves callers that cannot
+ * allocate device memory while they run: an application whose own pool
+ * allocator owns all device memory and forbids allocations behind its back,
+ * or a latency-bound loop where cudaFree's implicit device-wide
+ * synchronisation would stall its other streams.
+ *
+ * It computes exactly what cxbwt_build computes, with every intermediate
+ * buffer in one static device array of the library (about 34 MB, held by
+ * every GPU that loads the library until the process exits).  No context is
+ * needed and no memory is allocated: it calls no cudaMalloc, cudaFree,
+ * cudaMallocHost or other allocating routine.
+ *
+ *   reads_2bit      device pointer, packed bases (layout above)
+ *   lens_host       host pointer, n_reads lengths, all equal
+ *   out_bwt         device pointer, ceil(N / 16) words (as cxbwt_build)
+ *   out_dollar_pos  device pointer, n_reads entries (as cxbwt_build)
+ *   out_counts      device or host pointer, 5 entries (as cxbwt_build)
+ *   stream          cudaStream_t as void*; the call returns after the build
+ *                   has completed on it
+ *
+ * Limits: N = n_reads * (L + 1) <= CXBWT_NOALLOC_MAX_SUFFIXES and
+ * L <= CXBWT_NOALLOC_MAX_READ_LEN, one read length.  Returns CXBWT_OK;
+ * CXBWT_EINVAL for a NULL pointer, n_reads == 0 or a length of 0 or above
+ * 65535; CXBWT_EUNSUPPORTED for sizes beyond those limits or reads of
+ * different lengths (both checked before any device work); CXBWT_ECUDA,
+ * CXBWT_ETIMEOUT or CXBWT_EINTERNAL as cxbwt_build.
+ *
+ * The array is shared by every call on a device and keeps the previous
+ * call's contents (each call clears what must start at zero).  Calls whose
+ * device work overlaps - from two host threads, or on two streams without
+ * synchronisation between them - race on it: callers must serialise them.
+ * The first call on a device does that device's set-up (it looks up the
+ * array's device address and clears it); make it before any stream capture. */
+#define CXBWT_NOALLOC_MAX_SUFFIXES (1u << 21)
+#define CXBWT_NOALLOC_MAX_READ_LEN 272
+int cxbwt_build_noalloc(const uint32_t* reads_2bit, uint64_t n_reads, const uint32_t* lens_host, uint32_t* out_bwt,
+                        uint64_t* out_dollar_pos, uint64_t* out_counts, void* stream);
+
 /* ---- host helpers (no device work) ---------------------------------------- */
 
 /* Packs n_bases base codes (uint8 0..3) into ceil(n_bases/16) words, layout

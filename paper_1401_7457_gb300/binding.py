@@ -67,7 +67,22 @@ SIGNATURES = {
     "cxbwt_pack_codes": (ctypes.c_int, [_VP, _U64, _VP]),
     "cxbwt_pack_ascii": (ctypes.c_int, [ctypes.c_char_p, _U64, _VP]),
     "cxbwt_unpack_ascii": (ctypes.c_int, [_VP, _VP, _U64, _U64, _VP]),
+    "cxbwt_build_noalloc": (ctypes.c_int, [_VP, _U64, _VP, _VP, _VP, _VP, _VP]),
 }
+
+NOALLOC_MAX_SUFFIXES = 1 << 21
+NOALLOC_MAX_READ_LEN = 272
+
+
+def build_noalloc(reads_2bit, lens_host, out_bwt, out_dollar_pos, out_counts, stream=None):
+    """cxbwt_build_noalloc: device reads and outputs (torch CUDA tensors),
+    host lengths (numpy uint32).  Allocates nothing; raises CxbwtError on a
+    negative status."""
+    lens_host = np.ascontiguousarray(lens_host, dtype=np.uint32)
+    st = lib().cxbwt_build_noalloc(_ptr(reads_2bit), lens_host.size, lens_host.ctypes.data, _ptr(out_bwt),
+                                   _ptr(out_dollar_pos), _ptr(out_counts), _stream_ptr(stream))
+    if st != 0:
+        raise CxbwtError(st, "cxbwt_build_noalloc")
 
 
 def lib():
