@@ -22,199 +22,18 @@
 //   4. emission (Figure 2 step 3(c)(iii)); with host outputs, the finished
 //      words of each slice stream to the host on a side stream while the
 //      next slice sorts.
-#include <cuda_runtime.h>
-
-#include <algorithm>
-#include <cstdarg>
-#include <cstdio>
-#include <cstring>
-#include <mutex>
-#include <string>
-#include <vector>
-
-#include "../../include/cxbwt.h"
-#include "group.cuh"
-#include "kernels.cuh"
+#include "host.cuh"
 
 using namespace cxbwt;
+using namespace cxbwt::host;
 
 namespace {
-
 thread_local std::string g_create_error;
-
-struct DevBuf {
-  void* p = nullptr;
-  size_t cap = 0;
-};
-
-constexpr uint64_t kTimeoutNs = 1000000000ull;  // look-back waits give up after 1 s
-
 }  // namespace
 
-struct cxbwt_ctx {
-  cxbwt_options opt{};
-  int device = 0;
-  int sm_count = 0;
-  uint64_t budget = 0;
-  uint64_t held = 0;
-  std::string err;
 
-  DevBuf vals[2], keys[2], status, P, base, lenhist, desc, misc, store, out_bwt, out_dollar, out_sa, seglist, rhist,
-      bhist;
-  uint32_t epoch = 0;
-  cudaStream_t side = nullptr;            // device -> host streaming of finished slices
-  cudaEvent_t slice_done[2] = {nullptr, nullptr};
-  std::vector<cudaEvent_t> tev;           // timing events, 4 per slice (timing option)
-  unsigned long long* h_small = nullptr;  // pinned: device error word, length stats
-  cudaStream_t last_stream = nullptr;
-  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  cxbwt_stats stats{};
-};
-
-namespace {
-
-int fail(cxbwt_ctx* c, int status, const char* fmt, ...) {
-  char buf[512];
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(buf, sizeof buf, fmt, ap);
-  va_end(ap);
-  c->err = buf;
-  return status;
-}
-
-#define CX_CUDA(ctx, call)                                                                          \
-  do {                                                                                              \
-    cudaError_t e_ = (call);                                                                        \
-    if (e_ != cudaSuccess) {                                                                        \
-      return fail((ctx), e_ == cudaErrorMemoryAllocation ? CXBWT_ENOMEM : CXBWT_ECUDA, "%s: %s (%s:%d)", \
-                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                               \
-    }                                                                                               \
-  } while (0)
-
-#define CX_TRY(expr)          \
-  do {                        \
-    int s_ = (expr);          \
-    if (s_ != CXBWT_OK) return s_; \
-  } while (0)
-
-// Grow-only device buffer within the context's budget.
-int ensure(cxbwt_ctx* c, DevBuf& b, size_t bytes, const char* what) {
-  if (b.cap >= bytes) return CXBWT_OK;
-  // Large buffers grow in 2 MB steps (fewer regrows), small ones in 64 KB steps.
-  const size_t step = bytes >= (size_t(64) << 20) ? (size_t(1) << 21) : (size_t(1) << 16);
-  const size_t want = std::max<size_t>((bytes + step - 1) & ~(step - 1), step);
-  if (c->held - b.cap + want > c->budget)
-    return fail(c, CXBWT_ENOMEM, "device budget of %llu bytes exceeded growing %s to %zu bytes",
-                (unsigned long long)c->budget, what, want);
-  if (b.p) {
-    CX_CUDA(c, cudaFree(b.p));
-    c->held -= b.cap;
-    b.p = nullptr;
-    b.cap = 0;
-  }
-  void* p = nullptr;
-  cudaError_t e = cudaMalloc(&p, want);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(c, CXBWT_ENOMEM, "cudaMalloc(%zu) for %s: %s", want, what, cudaGetErrorString(e));
-  }
-  b.p = p;
-  b.cap = want;
-  c->held += want;
-  return CXBWT_OK;
-}
-
-void release(cxbwt_ctx* c, DevBuf& b) {
-  if (b.p) cudaFree(b.p);
-  c->held -= b.cap;
-  b.p = nullptr;
-  b.cap = 0;
-}
-
-bool is_device_ptr(const void* p) {
-  if (!p) return false;
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
-
-// misc buffer layout (bytes)
-constexpr size_t kMiscTileCounter = 0;   // uint32
-constexpr size_t kMiscErr = 4;           // uint32
-constexpr size_t kMiscCounts = 64;       // 5 x uint64
-constexpr size_t kMiscLenStats = 128;    // 4 x uint64
-constexpr size_t kMiscSeg = 192;         // 4 x uint32: group-finish list lengths and work counter
-constexpr size_t kMiscBytes = 256;
-
-uint32_t bits_for(uint32_t x) {  // smallest s with 2^s > x
-  uint32_t s = 0;
-  while (s < 32 && (uint64_t(1) << s) <= x) ++s;
-  return s;
-}
-
-constexpr uint32_t kBucketBits = 16;  // slices are ranges of buckets of the first 8 bases
-
-struct Plan {
-  uint64_t n = 0, sum = 0, N = 0;
-  uint32_t Lmin = 0, Lmax = 0, shift = 0;
-  bool uniform = true;
-  uint32_t D = 0;         // char digit positions (4 bases each)
-  uint32_t W = 0;         // 16-base windows
-  uint32_t len_passes = 0;
-  uint64_t n_words = 0;
-  int idb = 4;            // suffix id bytes
-  bool groups = false;
-  int seg_words = 0;
-  uint32_t w_last = 0;    // windows [0, w_last] are sorted by LSD passes over all rows of a slice
-};
-
-struct Slice {
-  bool whole = true;          // every suffix (no bucket filter)
-  uint32_t lo = 0, hi = 0;    // bucket range when not whole
-  uint32_t rows = 0;          // suffixes in the slice
-  uint64_t row0 = 0;          // global BWT row of its first suffix
-};
-
-// Per-build device state shared by the slices.
-struct Run {
-  cudaStream_t st = nullptr;
-  Plan pl;
-  ReadIndex R{};
-  TileShape shape{};
-  void* vals[2] = {nullptr, nullptr};
-  uint32_t* keys[2] = {nullptr, nullptr};
-  uint32_t* base = nullptr;
-  uint32_t* d_err = nullptr;
-  uint32_t* d_counter = nullptr;
-  uint32_t* d_seg = nullptr;
-  unsigned long long* d_counts = nullptr;
-  uint32_t* d_bwt = nullptr;      // global word w at d_bwt[w]
-  uint64_t* d_dollar = nullptr;
-  uint64_t* d_sa = nullptr;       // global rows
-  bool read_major = false;        // multi-slice first pass in read-major order
-  uint64_t launches = 0, sort_launches = 0, sort_items = 0, d2h = 0;
-};
-
-// Reads the device error word (already copied to h_small[4] by a completed
-// call), clears it, and turns it into a status.  The word is sticky on the
-// device until read here, so an error of an asynchronous build is not lost.
-int take_device_error(cxbwt_ctx* c) {
-  const uint32_t derr = *reinterpret_cast<volatile uint32_t*>(reinterpret_cast<char*>(c->h_small + 4));
-  if (!derr) return CXBWT_OK;
-  *reinterpret_cast<volatile uint32_t*>(reinterpret_cast<char*>(c->h_small + 4)) = 0;
-  CX_CUDA(c, cudaMemset(static_cast<char*>(c->misc.p) + kMiscErr, 0, 4));
-  if (derr & kErrTimeout)
-    return fail(c, CXBWT_ETIMEOUT, "a radix look-back wait exceeded %.1f s", double(kTimeoutNs) * 1e-9);
-  if (derr & kErrBounds)
-    return fail(c, CXBWT_EINTERNAL, "a sort pass or the emission met an out-of-range row or suffix id");
-  return fail(c, CXBWT_EINTERNAL, "device check failed (error word 0x%x)", derr);
-}
-
-void* vptr(void* base, int idb, uint64_t row) { return static_cast<char*>(base) + row * uint64_t(idb); }
+namespace cxbwt {
+namespace host {
 
 // Sort the slice's suffixes into r.vals[cur]; returns cur (0 or 1) through
 // *cur_out.  tev (or nullptr): events recorded before the digit passes and
@@ -780,7 +599,9 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   return CXBWT_OK;
 }
 
-}  // namespace
+}  // namespace host
+}  // namespace cxbwt
+
 
 extern "C" {
 
