@@ -177,6 +177,29 @@ int cxbwt_build_sa(cxbwt_ctx* ctx, const uint32_t* reads_2bit, uint64_t n_reads,
                    uint32_t* out_bwt, uint64_t* out_dollar_pos, uint64_t* out_counts, uint64_t* out_sa,
                    void* stream);
 
+/* One collection of a batch. */
+typedef struct {
+  const uint32_t* reads_2bit;   /* packed bases, host or device (layout above) */
+  uint64_t n_reads;
+  const uint32_t* lens;         /* n_reads lengths, host or device */
+  uint32_t* out_bwt;            /* as cxbwt_build */
+  uint64_t* out_dollar_pos;     /* as cxbwt_build, may be NULL */
+  uint64_t* out_counts;         /* as cxbwt_build, may be NULL */
+} cxbwt_collection;
+
+/* Builds the BWT of each of k independent collections (each result is
+ * exactly what cxbwt_build gives for that collection alone).  Collections of
+ * one read length are packed, up to a device-memory cap, into one sort: the
+ * sorted order of the union restricted to one collection is that
+ * collection's own order (the comparator of Section 2 is the same and the
+ * union keeps each collection's read order), so one set of launches sorts
+ * the pack, one stable pass by collection index separates it, and each
+ * collection is emitted from its contiguous rows.  Collections too large for
+ * a pack, or with reads of different lengths, are built one by one.
+ * Returns after every result is complete; on an error, results of
+ * collections not yet built are unspecified. */
+int cxbwt_build_batch(cxbwt_ctx* ctx, const cxbwt_collection* colls, uint64_t k, void* stream);
+
 /* Waits for the context's outstanding work and returns the first error a
  * device-side check recorded since the last call (CXBWT_OK if none). */
 int cxbwt_sync(cxbwt_ctx* ctx);

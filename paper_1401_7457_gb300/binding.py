@@ -68,7 +68,14 @@ SIGNATURES = {
     "cxbwt_pack_ascii": (ctypes.c_int, [ctypes.c_char_p, _U64, _VP]),
     "cxbwt_unpack_ascii": (ctypes.c_int, [_VP, _VP, _U64, _U64, _VP]),
     "cxbwt_build_noalloc": (ctypes.c_int, [_VP, _U64, _VP, _VP, _VP, _VP, _VP]),
+    "cxbwt_build_batch": (ctypes.c_int, [_VP, _VP, _U64, _VP]),
 }
+
+
+class Collection(ctypes.Structure):
+    """cxbwt_collection."""
+    _fields_ = [("reads_2bit", ctypes.c_void_p), ("n_reads", ctypes.c_uint64), ("lens", ctypes.c_void_p),
+                ("out_bwt", ctypes.c_void_p), ("out_dollar_pos", ctypes.c_void_p), ("out_counts", ctypes.c_void_p)]
 
 NOALLOC_MAX_SUFFIXES = 1 << 21
 NOALLOC_MAX_READ_LEN = 272
@@ -270,6 +277,18 @@ class Context:
                                _ptr(out_counts), st)
         _check(status, self._h)
         return out_bwt, out_dollar_pos, out_counts
+
+    def build_batch(self, collections, stream=None):
+        """collections: list of (reads_2bit, lens, out_bwt, out_dollar_pos, out_counts) arrays/tensors
+        (outputs required).  Builds every BWT; returns nothing (outputs are filled)."""
+        arr = (Collection * len(collections))()
+        keep = []
+        for i, (words, lens, bwt, dpos, cnt) in enumerate(collections):
+            n = int(lens.numel() if _is_tensor(lens) else np.asarray(lens).size)
+            arr[i] = Collection(_ptr(words), n, _ptr(lens), _ptr(bwt), _ptr(dpos), _ptr(cnt))
+            keep.append((words, lens, bwt, dpos, cnt))
+        _check(lib().cxbwt_build_batch(self._h, ctypes.cast(arr, ctypes.c_void_p), len(collections),
+                                       _stream_ptr(stream)), self._h)
 
     def sync(self):
         _check(lib().cxbwt_sync(self._h), self._h)

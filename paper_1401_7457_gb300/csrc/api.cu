@@ -522,6 +522,8 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
     e.sa_out = r.d_sa ? (sa_dev ? r.d_sa + sl.row0 : r.d_sa) : nullptr;
     e.err = r.d_err;
     e.id_bytes = pl.idb;
+    e.read_base = 0;
+    e.n_reads_out = uint32_t(n);
     CX_CUDA(c, launch_emit(e, st));
     ++r.launches;
     if (tev) CX_CUDA(c, cudaEventRecord(tev[3], st));

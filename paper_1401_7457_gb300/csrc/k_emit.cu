@@ -52,19 +52,19 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const EmitArgs a) {
       if (g >= a.row0 && g < end) {
         const Suffix s = decode(a.R, v[j]);
         uint32_t sym;
-        if (s.read >= a.R.n_reads || s.k > s.len) {
+        if (s.read - a.read_base >= a.n_reads_out || s.k > s.len) {
           atomicOr(a.err, kErrBounds);  // not a suffix id: record, write nothing through it
           sym = 0;
         } else if (s.k == 0) {
           sym = 0;  // $ is stored as code 0; its row is reported separately
           ++c[0];
-          if (a.dollar_pos) a.dollar_pos[s.read] = g;
+          if (a.dollar_pos) a.dollar_pos[s.read - a.read_base] = g;
         } else {
           sym = base_at(a.R, s.off + s.k - 1);
           ++c[sym + 1];
         }
         word |= sym << (30 - 2 * j);
-        if (a.sa_out) a.sa_out[g - a.row0] = (uint64_t(s.read) << 16) | s.k;
+        if (a.sa_out) a.sa_out[g - a.row0] = (uint64_t(s.read - a.read_base) << 16) | s.k;
       }
     }
     if (whole) a.bwt[w - a.word_base] = word;

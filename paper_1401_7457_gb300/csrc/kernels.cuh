@@ -23,7 +23,11 @@ enum SrcMode : int {
   // generated; the first window is gathered and carried; the digit is the
   // suffix length (at most 255).  Gathers walk the store in address order.
   kSrcInitReadMajor = 4,
+  // Ids are loaded; the digit is the index of the id's collection in a batch
+  // pack (coll_start: first read of each collection, ascending).
+  kSrcCollection = 5,
 };
+constexpr uint32_t kMaxPackCollections = 256;
 
 struct PassArgs {
   const void* vals_in;               // suffix ids (uint32 or uint64)
@@ -44,6 +48,8 @@ struct PassArgs {
   uint32_t n_reads;                  // generated modes
   uint32_t bucket_shift;             // filter: keep rows with (key >> bucket_shift) in [bucket_lo, bucket_hi)
   uint32_t bucket_lo, bucket_hi;
+  const uint32_t* coll_start;        // kSrcCollection: n_coll + 1 read starts
+  uint32_t n_coll;
   uint64_t timeout_ns;               // look-back wait limit
 };
 
@@ -95,6 +101,8 @@ struct EmitArgs {
   uint64_t* dollar_pos;      // per read (global rows), may be null
   unsigned long long* counts;// [5], accumulated
   uint64_t* sa_out;          // (i << 16) | k per slice row (sa_out[r]), may be null
+  uint32_t read_base;        // dollar_pos and sa_out use read index - read_base (a collection inside a pack)
+  uint32_t n_reads_out;      // reads of the slice's collection: read - read_base must be below it
   uint32_t* err;             // device error word
   int id_bytes;              // 4 or 8
 };

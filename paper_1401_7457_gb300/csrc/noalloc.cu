@@ -248,6 +248,8 @@ extern "C" int cxbwt_build_noalloc(const uint32_t* reads_2bit, uint64_t n_reads,
   e.sa_out = nullptr;
   e.err = d_err;
   e.id_bytes = 4;
+  e.read_base = 0;
+  e.n_reads_out = uint32_t(n_reads);
   NA_CUDA(launch_emit(e, st));
   {
     std::lock_guard<std::mutex> lock(g_mu);

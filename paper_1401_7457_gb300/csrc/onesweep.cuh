@@ -75,11 +75,14 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
   __shared__ uint32_t s_gbase[kRadix];  // global row of tile-local row 0 of each digit
   __shared__ uint32_t s_scan[8];
   __shared__ uint32_t s_tile, s_kept;
+  __shared__ uint32_t s_coll[MODE == kSrcCollection ? kMaxPackCollections + 1 : 1];
 
   const V* vals_in = static_cast<const V*>(a.vals_in);
   V* vals_out = static_cast<V*>(a.vals_out);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < WARPS * kRadix; i += THREADS) (&s_whist[0][0])[i] = 0u;
+  if (MODE == kSrcCollection)
+    for (uint32_t i = tid; i <= a.n_coll; i += THREADS) s_coll[i] = a.coll_start[i];
   if (tid == 0) {
     const uint32_t t = atomicAdd(a.tile_counter, 1u);
     // Every id has been handed out once the last one is: reset for the next pass.
@@ -152,6 +155,18 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
     for (int j = 0; j < IPT; ++j) {
       const Suffix s = decode(a.R, val[j]);
       key[j] = s.len - s.k;
+    }
+  } else if (MODE == kSrcCollection) {
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      // Collection of the id's read: the last c with s_coll[c] <= read.
+      const uint32_t read = uint32_t(val[j] >> a.R.shift);
+      uint32_t lo = 0, hi = a.n_coll;
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s_coll[mid] <= read) lo = mid; else hi = mid;
+      }
+      key[j] = lo;
     }
   } else {
 #pragma unroll
@@ -339,6 +354,9 @@ cudaError_t launch_shape(const PassArgs& a, int mode, bool wk, bool filter, cuda
     case kSrcLength:
       if (filter || wk) return cudaErrorInvalidValue;
       return launch_mode<V, S, kSrcLength, false, false>(a, st);
+    case kSrcCollection:
+      if (filter || wk) return cudaErrorInvalidValue;
+      return launch_mode<V, S, kSrcCollection, false, false>(a, st);
     default: return cudaErrorInvalidValue;
   }
 }
