@@ -31,8 +31,11 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const EmitArgs a) {
     // The slice owns the word when every row of it that exists is in the slice.
     const bool whole = g0 >= a.row0 && min(g0 + 16, a.n_total) <= end;
     V v[16];
-    if (whole && sizeof(V) == 4 && ((g0 - a.row0) & 15u) == 0) {
-      const uint4* p = reinterpret_cast<const uint4*>(reinterpret_cast<const uint32_t*>(sa) + (g0 - a.row0));
+    // 16-byte loads only when all 16 rows are in the slice and the address is
+    // 16-byte aligned (a collection inside a pack may start at any row).
+    const bool full16 = g0 >= a.row0 && g0 + 16 <= end;
+    if (full16 && sizeof(V) == 4 && (reinterpret_cast<uintptr_t>(sa + (g0 - a.row0)) & 15u) == 0) {
+      const uint4* p = reinterpret_cast<const uint4*>(sa + (g0 - a.row0));
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const uint4 x = __ldg(p + q);
