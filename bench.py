@@ -194,6 +194,68 @@ def run_reference(args, rank, world):
     return 0
 
 
+def run_batch_bench(args, rank, world):
+    """The batched workload: 256 collections (n log-uniform in [10k, 2M], read
+    length from {36, 76, 100, 150}, genome-like reads).  Times cxbwt_build_batch
+    against the plain loop of one cxbwt_build per collection, both on
+    device-resident inputs and outputs.  Prints one JSON line (not the
+    benchmark's default workload)."""
+    import torch
+
+    from paper_1401_7457_gb300 import binding, build, synth
+    build.build()
+    dev = torch.device("cuda", 0)
+    specs = synth.batch_specs()
+    if args.reads:
+        specs = specs[:args.reads]
+    colls, bases, suffixes = [], 0, 0
+    for sp in specs:
+        codes, lens = synth.batch_collection(sp)
+        words = binding.pack_codes(codes)
+        N = int(lens.sum()) + lens.size
+        colls.append((torch.from_numpy(words.view(np.int32)).to(dev), torch.from_numpy(lens.view(np.int32)).to(dev),
+                      torch.zeros((N + 15) // 16, dtype=torch.int32, device=dev),
+                      torch.zeros(lens.size, dtype=torch.int64, device=dev),
+                      torch.zeros(5, dtype=torch.int64, device=dev)))
+        bases += int(lens.sum())
+        suffixes += N
+    stream = torch.cuda.current_stream(dev)
+    ctx = binding.Context(device=0, budget_bytes=int(args.budget_gb * (1 << 30)))
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def plain():
+        for c in colls:
+            ctx.build(*c, stream=stream)
+
+    def batched():
+        ctx.build_batch(colls, stream=stream)
+
+    out = {}
+    for name, fn in (("plain", plain), ("batched", batched)):
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        out[name] = sum(ts) / len(ts)
+    ctx.close()
+    line = {"metric": METRIC, "value": bases / out["batched"] / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": out["batched"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"batched: {len(colls)} collections, {bases:,} bases, {suffixes:,} suffixes",
+                       "l2": "flushed between steps", "input": "device-resident"},
+            "plain_loop": {"value": bases / out["plain"] / 1e9, "unit": UNIT, "ms_per_step": out["plain"] * 1e3},
+            "speedup_vs_plain_loop": out["plain"] / out["batched"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -204,7 +266,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reads", type=int, default=0,
                     help="reads per GPU (0: the workload's own size; smaller only for profiling captures)")
-    ap.add_argument("--workload", default="genome-like", choices=sorted(WORKLOADS),
+    ap.add_argument("--workload", default="genome-like", choices=sorted(WORKLOADS) + ["batch"],
                     help="genome-like is the benchmark; the others are parity-test workloads timed for reference")
     ap.add_argument("--budget-gb", type=float, default=0.0,
                     help="device budget of the library context (0: 90%% of free memory)")
@@ -212,6 +274,8 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batch":
+        return run_batch_bench(args, rank, world)
 
     import torch
     import torch.distributed as dist
