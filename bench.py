@@ -256,6 +256,102 @@ def run_batch_bench(args, rank, world):
     return 0
 
 
+def run_serve_bench(args, rank, world):
+    """The served workload: 256 requests (n log-uniform in [50k, 5M], length 100
+    or 150, i.i.d. reads with per-request seeds) arriving as an open-loop
+    Poisson stream at 0.8x the plain loop's measured capacity.  The plain loop
+    builds one request at a time with cxbwt_build (pinned host buffers); its
+    latencies follow from its measured build times as a single FIFO server.
+    The served run submits each request at its arrival time to a cxbwt server
+    (continuous batching, 3 workers).  Prints one JSON line with p50/p99
+    latency and aggregate Gbase/s of both (not the benchmark's default line)."""
+    import threading
+
+    import torch
+
+    from paper_1401_7457_gb300 import binding, build, synth
+    build.build()
+    k = args.reads or 256
+    reqs = synth.serve_requests(k=k)
+    inputs = []
+    total_bases = 0
+    for rq in reqs:
+        codes, lens = synth.request_reads(rq)
+        words = torch.from_numpy(binding.pack_codes(codes).view(np.int32)).pin_memory()
+        lt = torch.from_numpy(lens.view(np.int32)).pin_memory()
+        N = int(lens.sum()) + lens.size
+        inputs.append((words, lt, N, lens.size))
+        total_bases += int(lens.sum())
+
+    def outputs(N, n):
+        return (torch.empty((N + 15) // 16, dtype=torch.int32).pin_memory(), torch.empty(n, dtype=torch.int64).pin_memory(),
+                torch.zeros(5, dtype=torch.int64).pin_memory())
+
+    # Plain loop: every request alone, back to back (service times).
+    ctx = binding.Context(device=0, budget_bytes=int(args.budget_gb * (1 << 30)))
+    warm = outputs(inputs[0][2], inputs[0][3])
+    ctx.build(inputs[0][0], inputs[0][1], *warm)
+    service = []
+    outs = [outputs(N, n) for (_, _, N, n) in inputs]
+    for (w, lt, N, n), o in zip(inputs, outs):
+        t0 = time.perf_counter()
+        ctx.build(w, lt, *o)
+        service.append(time.perf_counter() - t0)
+    ctx.close()
+    capacity = len(service) / sum(service)  # requests per second
+    rate = 0.8 * capacity
+    rng = np.random.default_rng(5)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(inputs)))
+    done, lat_plain = 0.0, []
+    for a, sv in zip(arrivals, service):
+        start = max(a, done)
+        done = start + sv
+        lat_plain.append((done - a) * 1e3)
+    plain_span = done - arrivals[0]
+
+    # Served: real-time submission at the arrival times.
+    outs2 = [outputs(N, n) for (_, _, N, n) in inputs]
+    srv = binding.Server(device=0, budget_bytes=int(args.budget_gb * (1 << 30)) or (120 << 30), workers=3)
+    warm_t = srv.submit(inputs[0][0], inputs[0][1], *outputs(inputs[0][2], inputs[0][3]))
+    srv.wait(warm_t)
+    tickets = [None] * len(inputs)
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, ((w, lt, N, n), o) in enumerate(zip(inputs, outs2)):
+            delay = arrivals[i] - arrivals[0] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets[i] = srv.submit(w, lt, *o)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    for t in tickets:
+        srv.wait(t)
+    span = time.perf_counter() - t0
+    lat_served = [srv.times(t)[1] for t in tickets]
+    counters = srv.counters()
+    srv.close()
+    # Every served result equals the plain loop's (the same build alone).
+    same = all(torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])
+               for a, b in zip(outs, outs2))
+    p = lambda xs, q: float(np.percentile(np.asarray(xs), q))
+    line = {"metric": METRIC, "value": total_bases / span / 1e9, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": f"served: {len(inputs)} requests, {total_bases:,} bases, Poisson arrivals at "
+                                   f"{rate:.1f}/s (0.8x the plain loop's {capacity:.1f}/s)", "workers": 3,
+                       "packs": counters["packs"]},
+            "served": {"p50_ms": p(lat_served, 50), "p99_ms": p(lat_served, 99),
+                       "gbase_per_s": total_bases / span / 1e9},
+            "plain_loop": {"p50_ms": p(lat_plain, 50), "p99_ms": p(lat_plain, 99),
+                           "gbase_per_s": total_bases / plain_span / 1e9},
+            "results_identical_to_alone": same}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -266,7 +362,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reads", type=int, default=0,
                     help="reads per GPU (0: the workload's own size; smaller only for profiling captures)")
-    ap.add_argument("--workload", default="genome-like", choices=sorted(WORKLOADS) + ["batch"],
+    ap.add_argument("--workload", default="genome-like", choices=sorted(WORKLOADS) + ["batch", "serve"],
                     help="genome-like is the benchmark; the others are parity-test workloads timed for reference")
     ap.add_argument("--budget-gb", type=float, default=0.0,
                     help="device budget of the library context (0: 90%% of free memory)")
@@ -276,6 +372,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "batch":
         return run_batch_bench(args, rank, world)
+    if args.workload == "serve":
+        return run_serve_bench(args, rank, world)
 
     import torch
     import torch.distributed as dist

@@ -200,6 +200,56 @@ typedef struct {
  * collections not yet built are unspecified. */
 int cxbwt_build_batch(cxbwt_ctx* ctx, const cxbwt_collection* colls, uint64_t k, void* stream);
 
+/* ---- serving: continuous batching of build requests --------------------------
+ *
+ * A server runs `workers` builds at once, each on its own context (its share
+ * of the device budget) and CUDA stream.  Requests queue in arrival order; a
+ * free worker takes the oldest one plus every queued request of the same read
+ * length that fits its pack cap (requests that arrive while others run join
+ * the next pack), builds them together (cxbwt_build_batch) and writes each
+ * result into the request's host buffers.  Every result is exactly what
+ * cxbwt_build gives for that request alone. */
+typedef struct cxbwt_server cxbwt_server;
+
+typedef struct {
+  uint64_t device_budget_bytes; /* device memory all workers may hold together; 0 = min(120 GB, 90% of free) */
+  int device;
+  int workers;                  /* concurrent builds; 0 = 3 */
+  uint64_t max_pack_suffixes;   /* suffixes built together at most; 0 = derived from the budget */
+  int reserved[8];
+} cxbwt_server_options;
+
+/* A request: every pointer is host memory that must stay valid (and, for the
+ * outputs, unread) until the request is done.  Pinned host memory makes the
+ * copies faster. */
+typedef struct {
+  const uint32_t* reads_2bit;   /* packed bases (layout above) */
+  uint64_t n_reads;
+  const uint32_t* lens;
+  uint32_t* out_bwt;            /* ceil(N / 16) words */
+  uint64_t* out_dollar_pos;     /* n_reads entries, may be NULL */
+  uint64_t* out_counts;         /* 5 entries, may be NULL */
+} cxbwt_request;
+
+void cxbwt_default_server_options(cxbwt_server_options* opt);
+/* Creates the server and starts its workers (each creates a context). */
+int cxbwt_server_create(cxbwt_server** out, const cxbwt_server_options* opt);
+/* Finishes every submitted request, stops the workers, frees everything. */
+void cxbwt_server_destroy(cxbwt_server* s);
+/* Queues a request; *ticket names it.  EINVAL for a bad request, EBUSY while
+ * the server is stopping.  Never blocks on the GPU.  Tickets (and their
+ * times) are kept until the server is destroyed. */
+int cxbwt_submit(cxbwt_server* s, const cxbwt_request* req, uint64_t* ticket);
+/* *done = 1 once the request finished (then returns its status), else 0 (returns CXBWT_OK). */
+int cxbwt_poll(cxbwt_server* s, uint64_t ticket, int* done);
+/* Blocks until the request finished; returns its status. */
+int cxbwt_wait(cxbwt_server* s, uint64_t ticket);
+/* Of a finished request: time from submission to the start of its build and
+ * to its completion (host clock, milliseconds).  EINVAL if not finished. */
+int cxbwt_ticket_times(cxbwt_server* s, uint64_t ticket, double* queued_ms, double* latency_ms);
+/* Requests completed, packs built, bases built so far (any pointer may be NULL). */
+int cxbwt_server_counters(cxbwt_server* s, uint64_t* completed, uint64_t* packs, uint64_t* bases);
+
 /* Waits for the context's outstanding work and returns the first error a
  * device-side check recorded since the last call (CXBWT_OK if none). */
 int cxbwt_sync(cxbwt_ctx* ctx);

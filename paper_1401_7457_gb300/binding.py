@@ -69,7 +69,92 @@ SIGNATURES = {
     "cxbwt_unpack_ascii": (ctypes.c_int, [_VP, _VP, _U64, _U64, _VP]),
     "cxbwt_build_noalloc": (ctypes.c_int, [_VP, _U64, _VP, _VP, _VP, _VP, _VP]),
     "cxbwt_build_batch": (ctypes.c_int, [_VP, _VP, _U64, _VP]),
+    "cxbwt_default_server_options": (None, [_VP]),
+    "cxbwt_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), _VP]),
+    "cxbwt_server_destroy": (None, [_VP]),
+    "cxbwt_submit": (ctypes.c_int, [_VP, _VP, ctypes.POINTER(ctypes.c_uint64)]),
+    "cxbwt_poll": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
+    "cxbwt_wait": (ctypes.c_int, [_VP, ctypes.c_uint64]),
+    "cxbwt_ticket_times": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]),
+    "cxbwt_server_counters": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                             ctypes.POINTER(ctypes.c_uint64)]),
 }
+
+
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("device_budget_bytes", ctypes.c_uint64), ("device", ctypes.c_int), ("workers", ctypes.c_int),
+                ("max_pack_suffixes", ctypes.c_uint64), ("reserved", ctypes.c_int * 8)]
+
+
+class Request(ctypes.Structure):
+    """cxbwt_request."""
+    _fields_ = [("reads_2bit", ctypes.c_void_p), ("n_reads", ctypes.c_uint64), ("lens", ctypes.c_void_p),
+                ("out_bwt", ctypes.c_void_p), ("out_dollar_pos", ctypes.c_void_p), ("out_counts", ctypes.c_void_p)]
+
+
+class Server:
+    """cxbwt_server: continuous batching of host-memory build requests."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0, workers: int = 0, max_pack_suffixes: int = 0):
+        L = lib()
+        opt = ServerOptions()
+        L.cxbwt_default_server_options(ctypes.byref(opt))
+        opt.device = device
+        opt.device_budget_bytes = budget_bytes
+        if workers:
+            opt.workers = workers
+        opt.max_pack_suffixes = max_pack_suffixes
+        h = ctypes.c_void_p()
+        _check(L.cxbwt_server_create(ctypes.byref(h), ctypes.byref(opt)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, reads_2bit, lens, out_bwt, out_dollar_pos=None, out_counts=None) -> int:
+        """Queue a request (host arrays, kept alive here until it is done); returns its ticket."""
+        lens_n = int(lens.numel() if _is_tensor(lens) else np.asarray(lens).size)
+        req = Request(_ptr(reads_2bit), lens_n, _ptr(lens), _ptr(out_bwt), _ptr(out_dollar_pos), _ptr(out_counts))
+        t = ctypes.c_uint64()
+        _check(lib().cxbwt_submit(self._h, ctypes.byref(req), ctypes.byref(t)))
+        self._keep[t.value] = (reads_2bit, lens, out_bwt, out_dollar_pos, out_counts)
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        done = ctypes.c_int()
+        _check(lib().cxbwt_poll(self._h, ticket, ctypes.byref(done)))
+        return bool(done.value)
+
+    def wait(self, ticket: int):
+        _check(lib().cxbwt_wait(self._h, ticket))
+
+    def times(self, ticket: int):
+        """(queued_ms, latency_ms) of a finished request."""
+        q, l = ctypes.c_double(), ctypes.c_double()
+        _check(lib().cxbwt_ticket_times(self._h, ticket, ctypes.byref(q), ctypes.byref(l)))
+        return q.value, l.value
+
+    def counters(self):
+        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().cxbwt_server_counters(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"completed": a.value, "packs": b.value, "bases": c.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cxbwt_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Collection(ctypes.Structure):

@@ -1,0 +1,72 @@
+"""Serving: requests submitted together are packed and built concurrently by
+several workers; every result equals the oracle's and the result of building
+that request alone."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_helpers import assert_same, oracle_of  # noqa: F401
+from paper_1401_7457_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def requests(k, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for r in range(k):
+        n = int(round(math.exp(rng.uniform(math.log(500), math.log(20_000)))))
+        L = int(synth.SERVE_LENGTHS[int(rng.integers(0, 2))])
+        out.append(synth.uniform_reads(n, L, synth.derive_seed(seed, r)))
+    return out
+
+
+def test_served_results_match_alone():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1401_7457_gb300 import binding
+    reqs = requests(40, 21)
+    reqs.insert(7, synth.mixed_length_reads(2000, 30, 150, 99))  # built alone inside a worker
+    outs = []
+    with binding.Server(device=0, workers=3) as srv:
+        tickets = []
+        for codes, lens in reqs:
+            words = binding.pack_codes(codes)
+            N = int(lens.sum()) + lens.size
+            bwt = np.zeros((N + 15) // 16, dtype=np.uint32)
+            dpos = np.zeros(lens.size, dtype=np.uint64)
+            cnt = np.zeros(5, dtype=np.uint64)
+            tickets.append(srv.submit(words, lens, bwt, dpos, cnt))
+            outs.append((N, bwt, dpos, cnt))
+        for t in tickets:
+            srv.wait(t)
+        lat = [srv.times(t)[1] for t in tickets]
+        counters = srv.counters()
+    assert counters["completed"] == len(reqs)
+    assert counters["packs"] < len(reqs)  # requests were built together
+    assert all(x > 0 for x in lat)
+    with binding.Context(device=0) as ctx:
+        for (codes, lens), (N, bwt, dpos, cnt) in zip(reqs, outs):
+            got = {"bwt": binding.unpack_ascii(bwt, dpos, N), "dollar_pos": dpos, "counts": cnt}
+            assert_same(got, oracle_of(codes, lens))
+            b, d, c = ctx.build(binding.pack_codes(codes), lens)
+            assert np.array_equal(b, bwt) and np.array_equal(d, dpos) and np.array_equal(c, cnt)
+
+
+def test_poll_and_bad_requests():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1401_7457_gb300 import binding
+    codes, lens = synth.uniform_reads(1000, 100, 5)
+    with binding.Server(device=0, workers=1) as srv:
+        bwt = np.zeros((101_000 + 15) // 16, dtype=np.uint32)
+        t = srv.submit(binding.pack_codes(codes), lens, bwt)
+        srv.wait(t)
+        assert srv.poll(t)
+        with pytest.raises(binding.CxbwtError):
+            srv.submit(binding.pack_codes(codes), np.zeros(3, dtype=np.uint32), bwt)
+    assert_same({"bwt": binding.unpack_ascii(bwt, oracle_of(codes, lens)["dollar_pos"], 101_000),
+                 "dollar_pos": oracle_of(codes, lens)["dollar_pos"], "counts": oracle_of(codes, lens)["counts"]},
+                oracle_of(codes, lens))
