@@ -671,6 +671,7 @@ int cxbwt_create(cxbwt_ctx** out, const cxbwt_options* opt) {
 
 void cxbwt_destroy(cxbwt_ctx* c) {
   if (!c) return;
+  if (c->batch_pool && c->batch_pool_free) c->batch_pool_free(c->batch_pool);
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   DevBuf* bufs[] = {&c->vals[0], &c->vals[1], &c->keys[0], &c->keys[1], &c->status, &c->P, &c->base,

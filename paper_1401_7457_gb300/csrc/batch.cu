@@ -1,8 +1,9 @@
-// cxbwt_build_batch: many independent collections, few launches.
+// cxbwt_build_batch: many independent collections, few launches, full GPU.
 //
-// Collections whose reads all have one length L (at most 272 bases) are
-// packed, in order, into "packs" of that length: up to 255 collections and a
-// device-memory cap of suffixes per pack.  A pack is built as one collection
+// Small collections (whose own builds would be bound by launch latency)
+// whose reads all have one length L (at most 272 bases) are packed, in
+// order, into "packs" of that length: up to 255 collections and a cap of
+// suffixes per pack.  A pack is built as one collection
 // whose reads are the packs' reads in order (read r of collection c is read
 // coll_start[c] + r of the pack): the comparator of Section 2 depends only
 // on the bases, the suffix length and the read order, so the pack's sorted
@@ -11,7 +12,14 @@
 // rows contiguous, and each collection is emitted from its rows (this is the
 // paper's merging of small partitions up to the GPU capacity, Section 3.1,
 // applied to whole collections).  Every other collection is built alone.
+// Packs and lone collections are then run, largest first, by a pool of
+// worker contexts (each with its own stream and a share of the budget), so
+// independent builds overlap on the GPU.
 #include <cuda_runtime.h>
+
+#include <condition_variable>
+#include <mutex>
+#include <thread>
 
 #include "host.cuh"
 
@@ -236,6 +244,112 @@ int build_pack(cxbwt_ctx* c, const cxbwt_collection* colls, const std::vector<ui
   return CXBWT_OK;
 }
 
+struct Item {
+  std::vector<uint32_t> colls;  // a pack (several) or one collection built alone
+  bool pack = false;
+  uint32_t L = 0;
+  uint64_t rows = 0;
+};
+
+// Worker contexts and threads of cxbwt_build_batch, kept by the context.
+struct Pool {
+  std::vector<cxbwt_ctx*> ctxs;
+  std::vector<cudaStream_t> streams;
+  std::vector<std::thread> threads;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  // the current batch
+  const cxbwt_collection* colls = nullptr;
+  const std::vector<Coll>* info = nullptr;
+  const std::vector<Item>* items = nullptr;
+  size_t next = 0, finished = 0;
+  int status = CXBWT_OK;
+  std::string err;
+  bool stop = false;
+  uint64_t generation = 0;
+};
+
+int run_item(cxbwt_ctx* c, const cxbwt_collection* colls, const std::vector<Coll>& info, const Item& it,
+             cudaStream_t st) {
+  if (it.pack) return build_pack(c, colls, it.colls, info, it.L, st);
+  const cxbwt_collection& col = colls[it.colls[0]];
+  return build_impl(c, col.reads_2bit, col.n_reads, col.lens, col.out_bwt, col.out_dollar_pos, col.out_counts,
+                    nullptr, st);
+}
+
+void pool_worker(Pool* p, int w) {
+  cxbwt_ctx* c = p->ctxs[w];
+  cudaSetDevice(c->device);
+  for (;;) {
+    const Item* it = nullptr;
+    {
+      std::unique_lock<std::mutex> lock(p->mu);
+      p->cv_work.wait(lock, [&] { return p->stop || (p->items && p->next < p->items->size()); });
+      if (p->stop) return;
+      it = &(*p->items)[p->next++];
+    }
+    int st = p->status == CXBWT_OK ? run_item(c, p->colls, *p->info, *it, p->streams[w]) : CXBWT_OK;
+    if (st == CXBWT_OK && cudaStreamSynchronize(p->streams[w]) != cudaSuccess) st = CXBWT_ECUDA;
+    {
+      std::lock_guard<std::mutex> lock(p->mu);
+      if (st != CXBWT_OK && p->status == CXBWT_OK) {
+        p->status = st;
+        p->err = c->err;
+      }
+      ++p->finished;
+    }
+    p->cv_done.notify_all();
+  }
+}
+
+void pool_free(void* v) {
+  auto* p = static_cast<Pool*>(v);
+  {
+    std::lock_guard<std::mutex> lock(p->mu);
+    p->stop = true;
+  }
+  p->cv_work.notify_all();
+  for (auto& t : p->threads) t.join();
+  for (auto* c : p->ctxs) cxbwt_destroy(c);
+  for (auto s : p->streams) cudaStreamDestroy(s);
+  delete p;
+}
+
+constexpr int kBatchWorkers = 3;
+
+int get_pool(cxbwt_ctx* c, Pool** out) {
+  if (c->batch_pool) {
+    *out = static_cast<Pool*>(c->batch_pool);
+    return CXBWT_OK;
+  }
+  auto* p = new Pool();
+  for (int w = 0; w < kBatchWorkers; ++w) {
+    cxbwt_options o = c->opt;
+    o.device_budget_bytes = c->budget / kBatchWorkers;
+    o.async = 0;
+    o.timing = 0;
+    cxbwt_ctx* wc = nullptr;
+    int st = cxbwt_create(&wc, &o);
+    cudaStream_t s = nullptr;
+    if (st == CXBWT_OK && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) st = CXBWT_ECUDA;
+    if (st != CXBWT_OK) {
+      if (wc) cxbwt_destroy(wc);
+      p->stop = true;
+      for (auto* x : p->ctxs) cxbwt_destroy(x);
+      for (auto x : p->streams) cudaStreamDestroy(x);
+      delete p;
+      return fail(c, st, "could not create the batch worker contexts: %s", cxbwt_last_error(nullptr));
+    }
+    p->ctxs.push_back(wc);
+    p->streams.push_back(s);
+  }
+  for (int w = 0; w < kBatchWorkers; ++w) p->threads.emplace_back(pool_worker, p, w);
+  c->batch_pool = p;
+  c->batch_pool_free = pool_free;
+  *out = p;
+  return CXBWT_OK;
+}
+
 }  // namespace
 
 extern "C" int cxbwt_build_batch(cxbwt_ctx* c, const cxbwt_collection* colls, uint64_t k, void* stream_v) {
@@ -271,35 +385,68 @@ extern "C" int cxbwt_build_batch(cxbwt_ctx* c, const cxbwt_collection* colls, ui
     }
     ci.N = ci.sum + ci.n;
   }
-  // Pack cap: a quarter of what the budget allows per suffix, at most 2^31 rows.
-  const uint64_t per_row = 2 * 8 + 8 + 1;
-  const uint64_t cap = std::min<uint64_t>(c->budget / per_row / 4, uint64_t(1) << 31);
-  std::vector<std::vector<uint32_t>> packs;  // by length, in collection order
-  std::vector<uint32_t> alone;
-  std::vector<std::vector<uint32_t>> open(65536);
-  std::vector<uint64_t> open_rows(65536, 0);
+  // Small collections (launch-bound alone) of one read length share packs;
+  // the rest are built alone.
+  const uint64_t small = uint64_t(8) << 20, pack_cap = uint64_t(64) << 20;
+  std::vector<Item> items;
+  std::vector<int64_t> open(65536, -1);
   for (uint32_t i = 0; i < k; ++i) {
     const Coll& ci = info[i];
-    if (!ci.uniform || !segsort_words(ci.L) || ci.N > cap / 2) {
-      alone.push_back(i);
+    if (!ci.uniform || !segsort_words(ci.L) || ci.N > small) {
+      Item it;
+      it.colls.push_back(i);
+      it.rows = ci.N;
+      items.push_back(it);
       continue;
     }
-    auto& p = open[ci.L];
-    if (!p.empty() && (open_rows[ci.L] + ci.N > cap || p.size() == kMaxPackCollections - 1)) {
-      packs.push_back(p);
-      p.clear();
-      open_rows[ci.L] = 0;
+    int64_t& o = open[ci.L];
+    if (o >= 0 && (items[o].rows + ci.N > pack_cap || items[o].colls.size() == kMaxPackCollections - 1)) o = -1;
+    if (o < 0) {
+      Item it;
+      it.pack = true;
+      it.L = ci.L;
+      items.push_back(it);
+      o = int64_t(items.size()) - 1;
     }
-    p.push_back(i);
-    open_rows[ci.L] += ci.N;
+    items[o].colls.push_back(i);
+    items[o].rows += ci.N;
   }
-  for (auto& p : open)
-    if (!p.empty()) packs.push_back(p);
-  for (const auto& p : packs) CX_TRY(build_pack(c, colls, p, info, info[p[0]].L, st));
-  for (uint32_t i : alone) {
-    const cxbwt_collection& col = colls[i];
-    CX_TRY(build_impl(c, col.reads_2bit, col.n_reads, col.lens, col.out_bwt, col.out_dollar_pos, col.out_counts,
-                      nullptr, stream_v));
+  // Largest first: the pool then finishes with the small ones.
+  std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.rows > b.rows; });
+  // Inputs may come from work queued on the caller's stream.
+  CX_CUDA(c, cudaStreamSynchronize(st));
+  Pool* p = nullptr;
+  CX_TRY(get_pool(c, &p));
+  {
+    std::lock_guard<std::mutex> lock(p->mu);
+    p->colls = colls;
+    p->info = &info;
+    p->items = &items;
+    p->next = 0;
+    p->finished = 0;
+    p->status = CXBWT_OK;
+    p->err.clear();
   }
-  return CXBWT_OK;
+  p->cv_work.notify_all();
+  int status;
+  {
+    std::unique_lock<std::mutex> lock(p->mu);
+    p->cv_done.wait(lock, [&] { return p->finished == items.size(); });
+    status = p->status;
+    if (status != CXBWT_OK) c->err = p->err;
+    p->items = nullptr;
+  }
+  for (auto* wc : p->ctxs) {
+    c->stats.builds += wc->stats.builds;
+    c->stats.bases += wc->stats.bases;
+    c->stats.suffixes += wc->stats.suffixes;
+    c->stats.kernel_launches += wc->stats.kernel_launches;
+    c->stats.sort_pass_launches += wc->stats.sort_pass_launches;
+    c->stats.sort_pass_items += wc->stats.sort_pass_items;
+    c->stats.h2d_bytes += wc->stats.h2d_bytes;
+    c->stats.d2h_bytes += wc->stats.d2h_bytes;
+    c->stats.slices += wc->stats.slices;
+    wc->stats = cxbwt_stats{};
+  }
+  return status;
 }

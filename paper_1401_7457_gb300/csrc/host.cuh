@@ -47,6 +47,8 @@ struct cxbwt_ctx {
   cudaStream_t last_stream = nullptr;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   cxbwt_stats stats{};
+  void* batch_pool = nullptr;             // worker contexts of cxbwt_build_batch (batch.cu), created on first use
+  void (*batch_pool_free)(void*) = nullptr;
 };
 
 namespace cxbwt {
