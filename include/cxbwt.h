@@ -82,7 +82,10 @@ typedef struct {
   int timing;                   /* nonzero: record CUDA events around every phase (see cxbwt_stats) */
   int algorithm;                /* CXBWT_ALGO_*: how the suffixes are sorted (all give identical output) */
   int plan_flags;               /* CXBWT_PLAN_* bits: force plan choices normally made by size (testing, tuning) */
-  int reserved[6];
+  int batch_workers;            /* cxbwt_build_batch: concurrent worker contexts (0 = automatic) */
+  int batch_small_mrows;        /* cxbwt_build_batch: collections below this many million suffixes are packed
+                                   (0 = automatic, -1 = never) */
+  int reserved[4];
 } cxbwt_options;
 
 /* plan_flags bits.  None changes the result.

@@ -34,7 +34,7 @@ class Options(ctypes.Structure):
     _fields_ = [("device_budget_bytes", ctypes.c_uint64), ("device", ctypes.c_int), ("prefix_len", ctypes.c_int),
                 ("digit_bits", ctypes.c_int), ("tile_items", ctypes.c_int), ("async_", ctypes.c_int),
                 ("timing", ctypes.c_int), ("algorithm", ctypes.c_int), ("plan_flags", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("batch_workers", ctypes.c_int), ("batch_small_mrows", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class Stats(ctypes.Structure):
@@ -279,7 +279,8 @@ class Context:
     PLAN_ID64, PLAN_READ_MAJOR = 1, 2
 
     def __init__(self, device: int = 0, budget_bytes: int = 0, async_: bool = False, timing: bool = False,
-                 tile_items: int = 0, algorithm: int = 0, plan_flags: int = 0):
+                 tile_items: int = 0, algorithm: int = 0, plan_flags: int = 0, batch_workers: int = 0,
+                 batch_small_mrows: int = 0):
         L = lib()
         opt = Options()
         L.cxbwt_default_options(ctypes.byref(opt))
@@ -290,6 +291,8 @@ class Context:
         opt.tile_items = tile_items
         opt.algorithm = algorithm
         opt.plan_flags = plan_flags
+        opt.batch_workers = batch_workers
+        opt.batch_small_mrows = batch_small_mrows
         h = ctypes.c_void_p()
         st = L.cxbwt_create(ctypes.byref(h), ctypes.byref(opt))
         if st != 0:

@@ -315,7 +315,7 @@ void pool_free(void* v) {
   delete p;
 }
 
-constexpr int kBatchWorkers = 3;
+constexpr int kMaxBatchWorkers = 8;
 
 int get_pool(cxbwt_ctx* c, Pool** out) {
   if (c->batch_pool) {
@@ -323,9 +323,10 @@ int get_pool(cxbwt_ctx* c, Pool** out) {
     return CXBWT_OK;
   }
   auto* p = new Pool();
-  for (int w = 0; w < kBatchWorkers; ++w) {
+  const int workers = std::min(std::max(c->opt.batch_workers ? c->opt.batch_workers : 2, 1), kMaxBatchWorkers);
+  for (int w = 0; w < workers; ++w) {
     cxbwt_options o = c->opt;
-    o.device_budget_bytes = c->budget / kBatchWorkers;
+    o.device_budget_bytes = c->budget / workers;
     o.async = 0;
     o.timing = 0;
     cxbwt_ctx* wc = nullptr;
@@ -343,7 +344,7 @@ int get_pool(cxbwt_ctx* c, Pool** out) {
     p->ctxs.push_back(wc);
     p->streams.push_back(s);
   }
-  for (int w = 0; w < kBatchWorkers; ++w) p->threads.emplace_back(pool_worker, p, w);
+  for (int w = 0; w < workers; ++w) p->threads.emplace_back(pool_worker, p, w);
   c->batch_pool = p;
   c->batch_pool_free = pool_free;
   *out = p;
@@ -387,7 +388,8 @@ extern "C" int cxbwt_build_batch(cxbwt_ctx* c, const cxbwt_collection* colls, ui
   }
   // Small collections (launch-bound alone) of one read length share packs;
   // the rest are built alone.
-  const uint64_t small = uint64_t(8) << 20, pack_cap = uint64_t(64) << 20;
+  const int sm = c->opt.batch_small_mrows;
+  const uint64_t small = sm < 0 ? 0 : uint64_t(sm ? sm : 8) << 20, pack_cap = std::max<uint64_t>(8 * small, 1);
   std::vector<Item> items;
   std::vector<int64_t> open(65536, -1);
   for (uint32_t i = 0; i < k; ++i) {
