@@ -361,21 +361,21 @@ extern "C" int cxbwt_build_batch(cxbwt_ctx* c, const cxbwt_collection* colls, ui
   CX_CUDA(c, cudaSetDevice(c->device));
   cudaStream_t st = static_cast<cudaStream_t>(stream_v);
   c->last_stream = st;
-  // Lengths of every collection (host copies of device lengths).
+  // Length statistics of every collection: host lengths are scanned here,
+  // device lengths by k_lenstats (one launch each, one copy back for all).
   std::vector<Coll> info(k);
-  std::vector<uint32_t> tmp;
+  std::vector<uint64_t> dev_idx;
   for (uint64_t i = 0; i < k; ++i) {
     const cxbwt_collection& col = colls[i];
     if (!col.reads_2bit || !col.lens || !col.out_bwt || col.n_reads == 0)
       return fail(c, CXBWT_EINVAL, "collection %llu: NULL pointer or no reads", (unsigned long long)i);
-    const uint32_t* h = col.lens;
-    if (is_device_ptr(col.lens)) {
-      tmp.resize(col.n_reads);
-      CX_CUDA(c, cudaMemcpy(tmp.data(), col.lens, col.n_reads * 4, cudaMemcpyDeviceToHost));
-      h = tmp.data();
-    }
     Coll& ci = info[i];
     ci.n = col.n_reads;
+    if (is_device_ptr(col.lens)) {
+      dev_idx.push_back(i);
+      continue;
+    }
+    const uint32_t* h = col.lens;
     ci.L = h[0];
     ci.uniform = true;
     for (uint64_t r = 0; r < col.n_reads; ++r) {
@@ -385,6 +385,31 @@ extern "C" int cxbwt_build_batch(cxbwt_ctx* c, const cxbwt_collection* colls, ui
       ci.sum += h[r];
     }
     ci.N = ci.sum + ci.n;
+  }
+  if (!dev_idx.empty()) {
+    const uint64_t m = dev_idx.size();
+    CX_TRY(ensure(c, c->rhist, m * 32, "length statistics"));
+    auto* d_ls = static_cast<unsigned long long*>(c->rhist.p);
+    std::vector<unsigned long long> ls(m * 4);
+    for (uint64_t j = 0; j < m; ++j) {
+      ls[4 * j] = ~0ull;
+      ls[4 * j + 1] = ls[4 * j + 2] = ls[4 * j + 3] = 0;
+    }
+    CX_CUDA(c, cudaMemcpyAsync(d_ls, ls.data(), m * 32, cudaMemcpyHostToDevice, st));
+    for (uint64_t j = 0; j < m; ++j)
+      CX_CUDA(c, launch_lenstats(colls[dev_idx[j]].lens, colls[dev_idx[j]].n_reads, d_ls + 4 * j, st));
+    CX_CUDA(c, cudaMemcpyAsync(ls.data(), d_ls, m * 32, cudaMemcpyDeviceToHost, st));
+    CX_CUDA(c, cudaStreamSynchronize(st));
+    for (uint64_t j = 0; j < m; ++j) {
+      Coll& ci = info[dev_idx[j]];
+      if (ls[4 * j + 3])
+        return fail(c, CXBWT_EINVAL, "collection %llu: a read length is 0 or above 65535",
+                    (unsigned long long)dev_idx[j]);
+      ci.L = uint32_t(ls[4 * j + 1]);
+      ci.uniform = ls[4 * j] == ls[4 * j + 1];
+      ci.sum = ls[4 * j + 2];
+      ci.N = ci.sum + ci.n;
+    }
   }
   // Small collections (launch-bound alone) of one read length share packs;
   // the rest are built alone.
