@@ -151,6 +151,20 @@ class ClockSampler:
                 "samples": len(rows), "reasons": reasons}
 
 
+def aggregate(dist, local_ms, bases_per_rank, world, steps):
+    """Whole-job throughput: bases of all ranks / the slowest rank's time.
+    Returns (gbase_per_s, max_ms).  With world == 1 no collective is used."""
+    total = local_ms
+    if world > 1:
+        import torch
+        t = torch.tensor([local_ms], dtype=torch.float64)
+        if dist.get_backend() == "nccl":
+            t = t.cuda()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    return bases_per_rank * world * steps / (total * 1e-3) / 1e9, total
+
+
 def cpu_oracle_rate(codes, lens, n_sample_reads, threads):
     """Oracle throughput on the first n_sample_reads reads: (Gbase/s, seconds, bases)."""
     import oracle
@@ -436,13 +450,8 @@ def main():
     if world > 1:
         dist.barrier()
     ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(ms)
     st = ctx.stats()
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = bases * world * args.steps / (total_ms * 1e-3) / 1e9
+    value, total_ms = aggregate(dist, sum(ms), bases, world, args.steps)
 
     # Dominant kernel: the onesweep digit pass.
     launches = max(st["sort_pass_launches"], 1)
@@ -480,12 +489,9 @@ def main():
         ctx2.build(h_words, h_lens, h_bwt, h_dpos, h_cnt, stream=stream)  # synchronous: returns with outputs on host
         t_e2e.append(time.perf_counter() - t0)
     st2 = ctx2.stats()
-    e2e_total = sum(t_e2e)
-    if world > 1:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e = {"value": bases * world * e2e_steps / e2e_total / 1e9, "unit": UNIT,
+    e2e_value, e2e_ms = aggregate(dist, sum(t_e2e) * 1e3, bases, world, e2e_steps)
+    e2e_total = e2e_ms * 1e-3
+    e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": st2["h2d_bytes"] // e2e_steps, "d2h_bytes_per_step": st2["d2h_bytes"] // e2e_steps,
            "ms_per_step": e2e_total / e2e_steps * 1e3, "steps": e2e_steps}
     ctx2.close()

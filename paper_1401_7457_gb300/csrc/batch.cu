@@ -323,7 +323,7 @@ int get_pool(cxbwt_ctx* c, Pool** out) {
     return CXBWT_OK;
   }
   auto* p = new Pool();
-  const int workers = std::min(std::max(c->opt.batch_workers ? c->opt.batch_workers : 2, 1), kMaxBatchWorkers);
+  const int workers = std::min(std::max(c->opt.batch_workers ? c->opt.batch_workers : 3, 1), kMaxBatchWorkers);
   for (int w = 0; w < workers; ++w) {
     cxbwt_options o = c->opt;
     o.device_budget_bytes = c->budget / workers;
@@ -414,7 +414,7 @@ extern "C" int cxbwt_build_batch(cxbwt_ctx* c, const cxbwt_collection* colls, ui
   // Small collections (launch-bound alone) of one read length share packs;
   // the rest are built alone.
   const int sm = c->opt.batch_small_mrows;
-  const uint64_t small = sm < 0 ? 0 : uint64_t(sm ? sm : 8) << 20, pack_cap = std::max<uint64_t>(8 * small, 1);
+  const uint64_t small = sm < 0 ? 0 : uint64_t(sm ? sm : 2) << 20, pack_cap = std::max<uint64_t>(8 * small, 1);
   std::vector<Item> items;
   std::vector<int64_t> open(65536, -1);
   for (uint32_t i = 0; i < k; ++i) {
