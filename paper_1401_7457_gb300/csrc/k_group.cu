@@ -106,57 +106,47 @@ __device__ __forceinline__ uint32_t suffix_len(const ReadIndex& R, V v) {
 // the front of their group; `need` is false for rows alone in their group.
 template <int NW>
 struct RowWords {
-  static constexpr int kPairs = (NW + 1) / 2;  // 64-bit words per row
-  unsigned long long r[32][kPairs];
+  static constexpr int kStride = (NW + 3) / 4 * 4;  // words per row, a whole number of uint4
+  uint4 r[32][kStride / 4];
 };
 
 template <int NW, class V>
 __device__ void warp_rank_window(const SegArgs& a, uint32_t cur, uint32_t n_rows, uint32_t gid, uint32_t gend,
                                  bool need, int lane, RowWords<NW>& sw) {
-  constexpr int P = RowWords<NW>::kPairs;
+  constexpr int Q = RowWords<NW>::kStride / 4;
   V* vals = static_cast<V*>(a.vals);
   const bool live = uint32_t(lane) < n_rows;
-  uint32_t w[2 * P];
-#pragma unroll
-  for (int i = 0; i < 2 * P; ++i) w[i] = 0u;
+  uint32_t w[Q * 4];
   V v = 0;
-  uint32_t pairs_needed = 0;  // 64-bit words holding real bases of this row
+#pragma unroll
+  for (int i = 0; i < Q * 4; ++i) w[i] = 0u;
   if (live) {
     v = vals[cur + lane];
     if (need) {
-      const Suffix sx = decode(a.R, v);
       uint32_t g[NW];
-      gather_words<NW>(a.R, sx, a.depth, g);
+      gather_words<NW>(a.R, decode(a.R, v), a.depth, g);
 #pragma unroll
       for (int i = 0; i < NW; ++i) w[i] = g[i];
-      const uint32_t rest = sx.len - sx.k > a.depth ? sx.len - sx.k - a.depth : 0u;
-      pairs_needed = min(uint32_t(P), (rest + 31u) / 32u);
     }
   }
-  // Publish this row's words for the other members of its group (most
-  // significant word in the high half, so 64-bit order is string order).
-  unsigned long long mine[P];
+  // Publish this row's words for the other members of its group.
 #pragma unroll
-  for (int q = 0; q < P; ++q) {
-    mine[q] = (static_cast<unsigned long long>(w[2 * q]) << 32) | w[2 * q + 1];
-    sw.r[lane][q] = mine[q];
-  }
-  // Words past every row's last base are zero in all rows: compare only the
-  // pairs some row of the window needs.
-  const uint32_t np = __reduce_max_sync(0xFFFFFFFFu, pairs_needed);
+  for (int q = 0; q < Q; ++q) sw.r[lane][q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
   __syncwarp();
   const uint32_t gsize = live ? gend - gid : 0u;
   uint32_t rank = 0;
   for (uint32_t t = 0; t < gsize; ++t) {
     const uint32_t src = gid + t;
-    // o < mine, lexicographic, with the row index breaking ties.
+    // o < w, lexicographic, with the row index breaking ties.
     bool lt = false, eq = true;
 #pragma unroll
-    for (int q = 0; q < P; ++q) {
-      if (uint32_t(q) < np) {
-        const unsigned long long o = sw.r[src][q];  // lanes of one group read one row: a broadcast
-        lt = lt || (eq && o < mine[q]);
-        eq = eq && (o == mine[q]);
+    for (int q = 0; q < Q; ++q) {
+      const uint4 o = sw.r[src][q];  // lanes of one group read one row: a broadcast
+      const uint32_t ov[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        lt = lt || (eq && ov[i] < w[4 * q + i]);
+        eq = eq && (ov[i] == w[4 * q + i]);
       }
     }
     lt = lt || (eq && src < uint32_t(lane));

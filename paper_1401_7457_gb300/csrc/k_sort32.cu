@@ -5,9 +5,7 @@
 namespace cxbwt {
 
 TileShape onesweep_shape(int tile_items_hint, int id_bytes) {
-  // 32-bit ids: 8192-item tiles unless 4096 is asked for (measured faster on
-  // GB300: fewer look-back steps per item).  64-bit ids: 4096.
-  if (id_bytes == 4 && tile_items_hint != 4096)
+  if (id_bytes == 4 && tile_items_hint == 8192)
     return TileShape{onesweep::ShapeLarge::threads, onesweep::ShapeLarge::ipt};
   return TileShape{onesweep::ShapeMid::threads, onesweep::ShapeMid::ipt};
 }

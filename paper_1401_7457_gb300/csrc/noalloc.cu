@@ -36,7 +36,7 @@ namespace {
 
 constexpr uint64_t kMaxRows = CXBWT_NOALLOC_MAX_SUFFIXES;
 constexpr uint32_t kMaxLen = CXBWT_NOALLOC_MAX_READ_LEN;
-constexpr uint32_t kTile = 4096;                       // onesweep_shape(4096, 4)
+constexpr uint32_t kTile = 4096;                       // onesweep_shape(0, 4)
 constexpr uint64_t kMaxTiles = (kMaxRows + kTile - 1) / kTile;
 constexpr uint32_t kMaxD = (kMaxLen + 3) / 4;
 constexpr uint32_t kMaxW = (kMaxLen + 15) / 16;
@@ -149,7 +149,7 @@ extern "C" int cxbwt_build_noalloc(const uint32_t* reads_2bit, uint64_t n_reads,
 
   void* vals[2] = {base + kOffVals0, base + kOffVals1};
   uint32_t* keys[2] = {reinterpret_cast<uint32_t*>(base + kOffKeys0), reinterpret_cast<uint32_t*>(base + kOffKeys1)};
-  const TileShape shape = onesweep_shape(4096, 4);
+  const TileShape shape = onesweep_shape(0, 4);
   PassArgs a{};
   a.status = reinterpret_cast<unsigned long long*>(base + kOffStatus);
   a.tile_counter = d_counter;

@@ -141,7 +141,7 @@ def test_budget_too_small_is_enomem():
         assert e.value.status == -2
 
 
-@pytest.mark.parametrize("tile_items", [4096, 8192])
+@pytest.mark.parametrize("tile_items", [2048, 4096, 8192])
 def test_tile_shapes_identical(tile_items):
     """The result does not depend on the tile shape of the digit passes."""
     from paper_1401_7457_gb300 import binding
