@@ -145,8 +145,10 @@ __device__ void warp_rank_window(const SegArgs& a, uint32_t cur, uint32_t n_rows
       const uint32_t ov[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        lt = lt || (eq && ov[i] < w[4 * q + i]);
-        eq = eq && (ov[i] == w[4 * q + i]);
+        if (4 * q + i < NW) {  // the padding words are zero in every row
+          lt = lt || (eq && ov[i] < w[4 * q + i]);
+          eq = eq && (ov[i] == w[4 * q + i]);
+        }
       }
     }
     lt = lt || (eq && src < uint32_t(lane));
@@ -380,6 +382,7 @@ cudaError_t launch_v(const SegArgs& a, int nw, int sm_count, cudaStream_t st) {
     case 4: return launch_nw<4, V>(a, sm_count, st);
     case 6: return launch_nw<6, V>(a, sm_count, st);
     case 8: return launch_nw<8, V>(a, sm_count, st);
+    case 10: return launch_nw<10, V>(a, sm_count, st);
     case 12: return launch_nw<12, V>(a, sm_count, st);
     case 16: return launch_nw<16, V>(a, sm_count, st);
     default: return cudaErrorInvalidValue;
@@ -395,6 +398,7 @@ int segsort_words(uint32_t max_len) {
   if (nw <= 4) return 4;
   if (nw <= 6) return 6;
   if (nw <= 8) return 8;
+  if (nw <= 10) return 10;
   if (nw <= 12) return 12;
   if (nw <= 16) return 16;
   return 0;  // reads too long for the on-chip finish
