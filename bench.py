@@ -63,7 +63,7 @@ def load_workload(name, rank=0, n_reads=0):
     return WORKLOADS[name], codes, lens
 SORT_BYTES_PER_ITEM = 16  # algorithmic bytes per suffix per digit pass: 4 B key + 4 B id, read and written
 PROFILE = os.path.join(ROOT, "profiles", "onesweep_digit_pass_genome_like.md")
-KERNEL_SRC = os.path.join(ROOT, "paper_1401_7457_gb300", "csrc", "k_sort.cu")
+KERNEL_SRC = os.path.join(ROOT, "paper_1401_7457_gb300", "csrc", "onesweep.cuh")
 FALLBACK_HBM_GBS = 6800.0
 
 
