@@ -25,7 +25,9 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const EmitArgs a) {
   const V* sa = static_cast<const V*>(a.sa);
   const uint64_t w = (a.row0 >> 4) + uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;  // global word
   const uint64_t end = a.row0 + a.n;
-  uint32_t c[5] = {0, 0, 0, 0, 0};
+  // Symbol counts of this thread's (at most 16) rows, 8 bits per symbol:
+  // byte 0 = $, bytes 1..4 = A, C, G, T.
+  unsigned long long cpack = 0;
   if (16 * w < end) {
     const uint64_t g0 = 16 * w;
     // The slice owns the word when every row of it that exists is in the slice.
@@ -60,11 +62,11 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const EmitArgs a) {
           sym = 0;
         } else if (s.k == 0) {
           sym = 0;  // $ is stored as code 0; its row is reported separately
-          ++c[0];
+          cpack += 1ull;
           if (a.dollar_pos) a.dollar_pos[s.read - a.read_base] = g;
         } else {
           sym = base_at(a.R, s.off + s.k - 1);
-          ++c[sym + 1];
+          cpack += 1ull << (8 * (sym + 1));
         }
         word |= sym << (30 - 2 * j);
         if (a.sa_out) a.sa_out[g - a.row0] = (uint64_t(s.read - a.read_base) << 16) | s.k;
@@ -75,7 +77,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const EmitArgs a) {
   }
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
-    const uint32_t x = __reduce_add_sync(0xFFFFFFFFu, c[q]);
+    const uint32_t x = __reduce_add_sync(0xFFFFFFFFu, uint32_t(cpack >> (8 * q)) & 0xFFu);
     if ((threadIdx.x & 31) == 0 && x) atomicAdd(&s_cnt[q], (unsigned long long)x);
   }
   __syncthreads();
