@@ -74,7 +74,6 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
   __shared__ uint32_t s_whist[WARPS][kRadix];
   __shared__ uint32_t s_gbase[kRadix];  // global row of tile-local row 0 of each digit
   __shared__ uint32_t s_scan[8];
-  __shared__ uint32_t s_tcnt[kRadix];  // this tile's count of each digit
   __shared__ uint32_t s_tile, s_kept;
   __shared__ uint32_t s_coll[MODE == kSrcCollection ? kMaxPackCollections + 1 : 1];
 
@@ -82,7 +81,6 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
   V* vals_out = static_cast<V*>(a.vals_out);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < WARPS * kRadix; i += THREADS) (&s_whist[0][0])[i] = 0u;
-  for (int i = tid; i < kRadix; i += THREADS) s_tcnt[i] = 0u;
   if (MODE == kSrcCollection)
     for (uint32_t i = tid; i <= a.n_coll; i += THREADS) s_coll[i] = a.coll_start[i];
   if (tid == 0) {
@@ -190,22 +188,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
     digit[j] = keep ? d : uint32_t(kRadix);
   }
 
-  // ---- 3a. tile counts first, published at once ----------------------------
-  // Successor tiles wait on these counts in their look-back; publishing them
-  // before the (longer) stable ranking keeps those waits short.
-#pragma unroll
-  for (int j = 0; j < IPT; ++j)
-    if (digit[j] < kRadix) atomicAdd(&s_tcnt[digit[j]], 1u);
-  __syncthreads();
-  uint32_t tile_cnt = 0;
-  if (tid < kRadix) {
-    tile_cnt = s_tcnt[tid];
-    const unsigned long long agg_flag = (unsigned long long)(2u * a.epoch) << 32;
-    const unsigned long long pre_flag = (unsigned long long)(2u * a.epoch + 1u) << 32;
-    store_relaxed_u64(a.status + uint64_t(tile) * kRadix + tid, (tile == 0 ? pre_flag : agg_flag) | tile_cnt);
-  }
-
-  // ---- 3b. stable rank inside the warp, in item order -----------------------
+  // ---- 3. stable rank inside the warp, in item order ------------------------
   // Lanes holding the same digit are found with one ballot per digit bit (a
   // 9th bit separates dropped rows: only in the last tile unless filtering):
   // cheaper on sm_103a than __match_any_sync.  digit[j] becomes
@@ -239,7 +222,8 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
   }
   __syncthreads();
 
-  // ---- 4. per-warp offsets, look-back ---------------------------------------
+  // ---- 4. tile counts, look-back --------------------------------------------
+  uint32_t tile_cnt = 0;
   if (tid < kRadix) {
     uint32_t sum = 0;
 #pragma unroll
@@ -248,6 +232,10 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
       s_whist[w][tid] = sum;
       sum += c;
     }
+    tile_cnt = sum;
+    const unsigned long long agg_flag = (unsigned long long)(2u * a.epoch) << 32;
+    const unsigned long long pre_flag = (unsigned long long)(2u * a.epoch + 1u) << 32;
+    store_relaxed_u64(a.status + uint64_t(tile) * kRadix + tid, (tile == 0 ? pre_flag : agg_flag) | tile_cnt);
   }
   const uint32_t local_excl = block_exclusive_scan_256<THREADS>(tile_cnt, s_scan);
   if (tid == kRadix - 1) s_kept = local_excl + tile_cnt;  // rows of this tile that are written
@@ -257,37 +245,15 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
     uint32_t before = 0;  // items with this digit in tiles 0 .. tile-1
     if (tile > 0) {
       const uint32_t agg = 2u * a.epoch, pre = 2u * a.epoch + 1u;
-      // Walk back over the predecessors, four status words per round trip:
-      // sum counts until an inclusive prefix is met; wait (bounded) on a word
-      // not yet published.
-      int64_t p = int64_t(tile) - 1;
+      uint32_t p = tile - 1;
       uint64_t t0 = 0;
       uint32_t spins = 0;
-      bool done = false;
-      while (!done && p >= 0) {
-        unsigned long long s4[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          s4[q] = (p - q >= 0) ? load_relaxed_u64(a.status + uint64_t(p - q) * kRadix + tid)
-                               : ((unsigned long long)pre << 32);
-        int used = 0;
-        bool stalled = false;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (done || stalled) continue;
-          const uint32_t flag = uint32_t(s4[q] >> 32);
-          if (flag != agg && flag != pre) {
-            stalled = true;  // tile p - q has not published yet: reload from it
-            continue;
-          }
-          if (p - q >= 0) before += uint32_t(s4[q]);
-          ++used;
-          if (flag == pre || p - q <= 0) done = true;
-        }
-        p -= used;
-        if (stalled) {
+      while (true) {
+        const unsigned long long s = load_relaxed_u64(a.status + uint64_t(p) * kRadix + tid);
+        const uint32_t flag = uint32_t(s >> 32);
+        if (flag != agg && flag != pre) {  // not yet published in this pass
           ++spins;
-          if (spins > 2) __nanosleep(64);
+          if (spins > 4) __nanosleep(64);
           if ((spins & 63u) == 0u) {
             const uint64_t now = global_timer_ns();
             if (t0 == 0) {
@@ -297,7 +263,11 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
               break;
             }
           }
+          continue;
         }
+        before += uint32_t(s);
+        if (flag == pre || p == 0) break;
+        --p;
       }
       store_relaxed_u64(a.status + uint64_t(tile) * kRadix + tid,
                         ((unsigned long long)(2u * a.epoch + 1u) << 32) | (before + tile_cnt));
