@@ -253,6 +253,24 @@ int cxbwt_ticket_times(cxbwt_server* s, uint64_t ticket, double* queued_ms, doub
 /* Requests completed, packs built, bases built so far (any pointer may be NULL). */
 int cxbwt_server_counters(cxbwt_server* s, uint64_t* completed, uint64_t* packs, uint64_t* bases);
 
+/* ---- autotuning -------------------------------------------------------------
+ * Times every candidate plan on one collection (device or host buffers) and
+ * keeps the fastest in the context for builds of the same maximum read
+ * length and size class (N within a factor of two) whose options leave
+ * tile_items and algorithm automatic.  Candidates: tiles of 4096 or 8192
+ * items x the group plan (reads of at most 272 bases) or the LSD plan.  The
+ * radix digit is 8 bits (the only width built).  scratch_bwt (ceil(N / 16)
+ * words) and scratch_dollar_pos (n_reads, may be NULL) receive the BWT;
+ * every candidate produces the same one. */
+typedef struct {
+  int tile_items;
+  int algorithm;   /* CXBWT_ALGO_GROUPS or CXBWT_ALGO_LSD */
+  int digit_bits;
+  float best_ms;   /* device time of one build with the chosen plan */
+} cxbwt_tuning;
+int cxbwt_autotune(cxbwt_ctx* ctx, const uint32_t* reads_2bit, uint64_t n_reads, const uint32_t* lens,
+                   uint32_t* scratch_bwt, uint64_t* scratch_dollar_pos, void* stream, cxbwt_tuning* out);
+
 /* Waits for the context's outstanding work and returns the first error a
  * device-side check recorded since the last call (CXBWT_OK if none). */
 int cxbwt_sync(cxbwt_ctx* ctx);

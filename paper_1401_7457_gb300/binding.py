@@ -69,6 +69,7 @@ SIGNATURES = {
     "cxbwt_unpack_ascii": (ctypes.c_int, [_VP, _VP, _U64, _U64, _VP]),
     "cxbwt_build_noalloc": (ctypes.c_int, [_VP, _U64, _VP, _VP, _VP, _VP, _VP]),
     "cxbwt_build_batch": (ctypes.c_int, [_VP, _VP, _U64, _VP]),
+    "cxbwt_autotune": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP, _VP, _VP, _VP]),
     "cxbwt_default_server_options": (None, [_VP]),
     "cxbwt_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), _VP]),
     "cxbwt_server_destroy": (None, [_VP]),
@@ -80,6 +81,11 @@ SIGNATURES = {
     "cxbwt_server_counters": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                              ctypes.POINTER(ctypes.c_uint64)]),
 }
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("tile_items", ctypes.c_int), ("algorithm", ctypes.c_int), ("digit_bits", ctypes.c_int),
+                ("best_ms", ctypes.c_float)]
 
 
 class ServerOptions(ctypes.Structure):
@@ -377,6 +383,15 @@ class Context:
             keep.append((words, lens, bwt, dpos, cnt))
         _check(lib().cxbwt_build_batch(self._h, ctypes.cast(arr, ctypes.c_void_p), len(collections),
                                        _stream_ptr(stream)), self._h)
+
+    def autotune(self, reads_2bit, lens, scratch_bwt, scratch_dollar_pos=None, stream=None) -> dict:
+        """Time the candidate plans on this collection; later builds of its size class use the fastest."""
+        n = int(lens.numel() if _is_tensor(lens) else np.asarray(lens).size)
+        t = Tuning()
+        _check(lib().cxbwt_autotune(self._h, _ptr(reads_2bit), n, _ptr(lens), _ptr(scratch_bwt),
+                                    _ptr(scratch_dollar_pos), _stream_ptr(stream), ctypes.byref(t)), self._h)
+        return {"tile_items": t.tile_items, "algorithm": t.algorithm, "digit_bits": t.digit_bits,
+                "best_ms": t.best_ms}
 
     def sync(self):
         _check(lib().cxbwt_sync(self._h), self._h)

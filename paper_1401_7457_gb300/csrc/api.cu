@@ -291,14 +291,22 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   pl.len_passes = pl.uniform ? 0 : (pl.Lmax > 255 ? 2 : 1);
   pl.n_words = (sum + 15) / 16;
   pl.seg_words = segsort_words(pl.Lmax);
-  switch (c->opt.algorithm) {
+  int algorithm = c->opt.algorithm, tile_items = c->opt.tile_items;
+  {
+    int t_tile = 0, t_algo = 0;
+    if (tuned_choice(c, pl.Lmax, pl.N, &t_tile, &t_algo)) {
+      if (algorithm == CXBWT_ALGO_AUTO) algorithm = t_algo;
+      if (tile_items == 0) tile_items = t_tile;
+    }
+  }
+  switch (algorithm) {
     case CXBWT_ALGO_LSD: pl.groups = false; break;
     case CXBWT_ALGO_GROUPS:
       if (!pl.seg_words) return fail(c, CXBWT_EUNSUPPORTED, "the group plan handles reads of at most 272 bases");
       pl.groups = true;
       break;
     case CXBWT_ALGO_AUTO: pl.groups = pl.seg_words != 0; break;
-    default: return fail(c, CXBWT_EINVAL, "unknown algorithm %d", c->opt.algorithm);
+    default: return fail(c, CXBWT_EINVAL, "unknown algorithm %d", algorithm);
   }
   // Windows [0, w_last] are sorted by LSD passes over all rows; with the
   // group plan only window 0 is, and the groups are finished on chip.
@@ -306,7 +314,7 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   const uint64_t max_id = ((n - 1) << pl.shift) | pl.Lmax;
   pl.idb = (pl.shift <= 31 && ((n - 1) >> (32 - pl.shift)) == 0 && max_id <= 0xFFFFFFFFull) ? 4 : 8;
   if (c->opt.plan_flags & CXBWT_PLAN_ID64) pl.idb = 8;
-  r.shape = onesweep_shape(c->opt.tile_items, pl.idb);
+  r.shape = onesweep_shape(tile_items, pl.idb);
   const uint32_t TILE = uint32_t(r.shape.tile());
 
   // ---- inputs on the device ----------------------------------------------

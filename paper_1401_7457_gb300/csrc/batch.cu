@@ -444,6 +444,7 @@ extern "C" int cxbwt_build_batch(cxbwt_ctx* c, const cxbwt_collection* colls, ui
   CX_CUDA(c, cudaStreamSynchronize(st));
   Pool* p = nullptr;
   CX_TRY(get_pool(c, &p));
+  for (auto* wc : p->ctxs) wc->tuned = c->tuned;  // the workers build with the context's autotuned plans
   {
     std::lock_guard<std::mutex> lock(p->mu);
     p->colls = colls;

@@ -47,6 +47,9 @@ struct cxbwt_ctx {
   cudaStream_t last_stream = nullptr;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   cxbwt_stats stats{};
+  // Autotuner choices (autotune.cu): key (max read length << 8 | log2 N class)
+  // -> (tile items, algorithm).  Used when the options leave them automatic.
+  std::vector<std::pair<uint64_t, std::pair<int, int>>> tuned;
   void* batch_pool = nullptr;             // worker contexts of cxbwt_build_batch (batch.cu), created on first use
   void (*batch_pool_free)(void*) = nullptr;
 };
@@ -196,6 +199,24 @@ inline int take_device_error(cxbwt_ctx* c) {
 }
 
 inline void* vptr(void* base, int idb, uint64_t row) { return static_cast<char*>(base) + row * uint64_t(idb); }
+
+inline uint64_t tune_key(uint32_t max_len, uint64_t n_suffixes) {
+  uint32_t cls = 0;
+  while (cls < 63 && (uint64_t(1) << (cls + 1)) <= n_suffixes) ++cls;
+  return (uint64_t(max_len) << 8) | cls;
+}
+
+// The autotuned (tile items, algorithm) of a build, or false.
+inline bool tuned_choice(const cxbwt_ctx* c, uint32_t max_len, uint64_t n_suffixes, int* tile, int* algo) {
+  const uint64_t k = tune_key(max_len, n_suffixes);
+  for (const auto& e : c->tuned)
+    if (e.first == k) {
+      *tile = e.second.first;
+      *algo = e.second.second;
+      return true;
+    }
+  return false;
+}
 
 // Sort one slice into r.vals[*cur_out] (api.cu).
 int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t* tev);

@@ -204,3 +204,23 @@ def test_group_plan_rejects_long_reads():
         assert e.value.status == -5
     with binding.Context(device=0) as c:  # the automatic plan takes the LSD passes instead
         assert_same(gpu_bwt(c, codes, lens), oracle_of(codes, lens))
+
+
+def test_autotune_then_build():
+    """The autotuner picks a plan on one collection; builds of that size class
+    use it and still equal the oracle."""
+    from paper_1401_7457_gb300 import binding
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    codes, lens = synth.sample_reads(synth.random_genome(40_000, 81), 12_000, 100, 82, 0.01)
+    N = int(lens.sum()) + lens.size
+    words = torch.from_numpy(binding.pack_codes(codes).view(np.int32)).cuda()
+    dl = torch.from_numpy(lens.view(np.int32)).cuda()
+    scratch = torch.zeros((N + 15) // 16, dtype=torch.int32, device="cuda")
+    with binding.Context(device=0) as c:
+        t = c.autotune(words, dl, scratch)
+        assert t["tile_items"] in (4096, 8192) and t["algorithm"] in (1, 2) and t["best_ms"] > 0
+        assert_same(gpu_bwt(c, codes, lens), oracle_of(codes, lens))
+        # same size class, other data
+        codes2, lens2 = synth.uniform_reads(12_000, 100, 83)
+        assert_same(gpu_bwt(c, codes2, lens2), oracle_of(codes2, lens2))
