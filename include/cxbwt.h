@@ -85,7 +85,8 @@ typedef struct {
   int batch_workers;            /* cxbwt_build_batch: concurrent worker contexts (0 = automatic) */
   int batch_small_mrows;        /* cxbwt_build_batch: collections below this many million suffixes are packed
                                    (0 = automatic, -1 = never) */
-  int reserved[4];
+  int wait_limit_ms;            /* limit of every device-side wait (radix look-back); 0 = 1000 ms */
+  int reserved[3];
 } cxbwt_options;
 
 /* plan_flags bits.  None changes the result.
@@ -95,6 +96,11 @@ typedef struct {
  *                store would fit L2. */
 #define CXBWT_PLAN_ID64 1
 #define CXBWT_PLAN_READ_MAJOR 2
+/* Test hook for failure handling: in the first digit pass of a build, tile 0
+ * does not publish its counts, so tile 1's look-back wait runs out (after
+ * wait_limit_ms).  The build then returns CXBWT_ETIMEOUT with unspecified
+ * outputs; nothing hangs or faults and the context stays usable. */
+#define CXBWT_PLAN_TEST_STALL 4
 
 /* Sort plans.  Every plan computes the same B_R; they differ in speed only.
  *  AUTO     - GROUPS when the reads are at most 272 bases, else LSD.

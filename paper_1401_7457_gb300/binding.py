@@ -34,7 +34,8 @@ class Options(ctypes.Structure):
     _fields_ = [("device_budget_bytes", ctypes.c_uint64), ("device", ctypes.c_int), ("prefix_len", ctypes.c_int),
                 ("digit_bits", ctypes.c_int), ("tile_items", ctypes.c_int), ("async_", ctypes.c_int),
                 ("timing", ctypes.c_int), ("algorithm", ctypes.c_int), ("plan_flags", ctypes.c_int),
-                ("batch_workers", ctypes.c_int), ("batch_small_mrows", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("batch_workers", ctypes.c_int), ("batch_small_mrows", ctypes.c_int), ("wait_limit_ms", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 class Stats(ctypes.Structure):
@@ -282,11 +283,11 @@ class Context:
     """One cxbwt context (device workspace + bookkeeping) on one device."""
 
     ALGO_AUTO, ALGO_LSD, ALGO_GROUPS = 0, 1, 2
-    PLAN_ID64, PLAN_READ_MAJOR = 1, 2
+    PLAN_ID64, PLAN_READ_MAJOR, PLAN_TEST_STALL = 1, 2, 4
 
     def __init__(self, device: int = 0, budget_bytes: int = 0, async_: bool = False, timing: bool = False,
                  tile_items: int = 0, algorithm: int = 0, plan_flags: int = 0, batch_workers: int = 0,
-                 batch_small_mrows: int = 0):
+                 batch_small_mrows: int = 0, wait_limit_ms: int = 0):
         L = lib()
         opt = Options()
         L.cxbwt_default_options(ctypes.byref(opt))
@@ -299,6 +300,7 @@ class Context:
         opt.plan_flags = plan_flags
         opt.batch_workers = batch_workers
         opt.batch_small_mrows = batch_small_mrows
+        opt.wait_limit_ms = wait_limit_ms
         h = ctypes.c_void_p()
         st = L.cxbwt_create(ctypes.byref(h), ctypes.byref(opt))
         if st != 0:

@@ -48,7 +48,7 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
   a.err = r.d_err;
   a.R = r.R;
   a.n_reads = uint32_t(pl.n);
-  a.timeout_ns = kTimeoutNs;
+  a.timeout_ns = c->opt.wait_limit_ms > 0 ? uint64_t(c->opt.wait_limit_ms) * 1000000ull : kTimeoutNs;
   a.bucket_shift = 32 - kBucketBits;
   a.bucket_lo = sl.lo;
   a.bucket_hi = sl.hi;
@@ -140,7 +140,9 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
       a.key_shift = 24u - 8u * uint32_t(d - d_lo);
       a.window_c0 = uint32_t(16 * w);
       a.epoch = ++c->epoch;
+      a.stall_tile0 = (c->opt.plan_flags & CXBWT_PLAN_TEST_STALL) && r.sort_launches == 0 ? 1u : 0u;
       CX_CUDA(c, launch_onesweep(a, mode, write_key, generated && !sl.whole, idb, r.shape, st));
+      a.stall_tile0 = 0;
       cur ^= 1;
       if (write_key) kin = kout;
       first = false;

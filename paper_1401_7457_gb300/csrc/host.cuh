@@ -191,8 +191,7 @@ inline int take_device_error(cxbwt_ctx* c) {
   if (!derr) return CXBWT_OK;
   *reinterpret_cast<volatile uint32_t*>(reinterpret_cast<char*>(c->h_small + 4)) = 0;
   CX_CUDA(c, cudaMemset(static_cast<char*>(c->misc.p) + kMiscErr, 0, 4));
-  if (derr & kErrTimeout)
-    return fail(c, CXBWT_ETIMEOUT, "a radix look-back wait exceeded %.1f s", double(kTimeoutNs) * 1e-9);
+  if (derr & kErrTimeout) return fail(c, CXBWT_ETIMEOUT, "a radix look-back wait exceeded its limit");
   if (derr & kErrBounds)
     return fail(c, CXBWT_EINTERNAL, "a sort pass or the emission met an out-of-range row or suffix id");
   return fail(c, CXBWT_EINTERNAL, "device check failed (error word 0x%x)", derr);

@@ -50,6 +50,7 @@ struct PassArgs {
   uint32_t bucket_lo, bucket_hi;
   const uint32_t* coll_start;        // kSrcCollection: n_coll + 1 read starts
   uint32_t n_coll;
+  uint32_t stall_tile0;              // test hook: tile 0 publishes nothing (its successor's wait runs out)
   uint64_t timeout_ns;               // look-back wait limit
 };
 

@@ -235,7 +235,8 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
     tile_cnt = sum;
     const unsigned long long agg_flag = (unsigned long long)(2u * a.epoch) << 32;
     const unsigned long long pre_flag = (unsigned long long)(2u * a.epoch + 1u) << 32;
-    store_relaxed_u64(a.status + uint64_t(tile) * kRadix + tid, (tile == 0 ? pre_flag : agg_flag) | tile_cnt);
+    if (!(tile == 0 && a.stall_tile0))
+      store_relaxed_u64(a.status + uint64_t(tile) * kRadix + tid, (tile == 0 ? pre_flag : agg_flag) | tile_cnt);
   }
   const uint32_t local_excl = block_exclusive_scan_256<THREADS>(tile_cnt, s_scan);
   if (tid == kRadix - 1) s_kept = local_excl + tile_cnt;  // rows of this tile that are written
@@ -271,6 +272,8 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
       }
       store_relaxed_u64(a.status + uint64_t(tile) * kRadix + tid,
                         ((unsigned long long)(2u * a.epoch + 1u) << 32) | (before + tile_cnt));
+      // (after a wait that ran out, `before` is short: the outputs are then
+      // unspecified but every write stays in bounds, and the error word says so)
     }
     s_gbase[tid] = __ldg(a.digit_base + tid) + before - local_excl;
   }
