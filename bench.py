@@ -376,6 +376,55 @@ def run_serve_bench(args, rank, world):
     return 0
 
 
+def run_length_bench(args, rank, world):
+    """Read-length sensitivity at equal total bases (after Table exp-len of the
+    paper: 100/200/400 bp): genome-like reads from the 5 Mbp genome at 20x,
+    1M x 100, 500k x 200 and 250k x 400 bp.  One JSON line with Gbase/s per
+    length (not the benchmark's default line)."""
+    import torch
+
+    from paper_1401_7457_gb300 import binding, build, synth
+    build.build()
+    dev = torch.device("cuda", 0)
+    g = synth.random_genome(5_000_000, 2)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    res = {}
+    for L, n in ((100, 1_000_000), (200, 500_000), (400, 250_000)):
+        codes, lens = synth.sample_reads(g, n, L, synth.derive_seed(2, L), 0.01)
+        w = torch.from_numpy(binding.pack_codes(codes).view(np.int32)).to(dev)
+        ln = torch.from_numpy(lens.view(np.int32)).to(dev)
+        ctx = binding.Context(device=0, timing=True)
+        outs = ctx.build(w, ln)
+        for _ in range(max(args.warmup, 1)):
+            ctx.build(w, ln, *outs)
+        ctx.reset_stats()
+        ts = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.build(w, ln, *outs)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        st = ctx.stats()
+        ms = sum(ts) / len(ts)
+        res[f"{L}bp"] = {"reads": n, "ms": ms, "gbase_per_s": n * L / (ms * 1e-3) / 1e9,
+                         "group_finish_ms": st["group_ms"] / len(ts), "sort_pass_ms": st["sort_pass_ms"] / len(ts)}
+        ctx.close()
+    base = res["100bp"]["ms"]
+    for k in res:
+        res[k]["time_vs_100bp"] = res[k]["ms"] / base
+    line = {"metric": METRIC, "value": res["100bp"]["gbase_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": base, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "read-length series: 100 Mbase of genome-like reads at 100, 200 and 400 bp"},
+            "lengths": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -386,7 +435,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reads", type=int, default=0,
                     help="reads per GPU (0: the workload's own size; smaller only for profiling captures)")
-    ap.add_argument("--workload", default="genome-like", choices=sorted(WORKLOADS) + ["batch", "serve"],
+    ap.add_argument("--workload", default="genome-like", choices=sorted(WORKLOADS) + ["batch", "serve", "length"],
                     help="genome-like is the benchmark; the others are parity-test workloads timed for reference")
     ap.add_argument("--budget-gb", type=float, default=0.0,
                     help="device budget of the library context (0: 90%% of free memory)")
@@ -398,6 +447,8 @@ def main():
         return run_batch_bench(args, rank, world)
     if args.workload == "serve":
         return run_serve_bench(args, rank, world)
+    if args.workload == "length":
+        return run_length_bench(args, rank, world)
 
     import torch
     import torch.distributed as dist

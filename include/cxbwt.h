@@ -103,7 +103,7 @@ typedef struct {
 #define CXBWT_PLAN_TEST_STALL 4
 
 /* Sort plans.  Every plan computes the same B_R; they differ in speed only.
- *  AUTO     - GROUPS when the reads are at most 272 bases, else LSD.
+ *  AUTO     - GROUPS when the reads are at most 528 bases, else LSD.
  *  LSD      - stable LSD radix passes over every 4-base digit of the
  *             A-padded suffixes (Section 3.2 as stated: one pass per digit).
  *  GROUPS   - LSD passes over the first 16 bases only (the l-prefix
@@ -264,7 +264,7 @@ int cxbwt_server_counters(cxbwt_server* s, uint64_t* completed, uint64_t* packs,
  * keeps the fastest in the context for builds of the same maximum read
  * length and size class (N within a factor of two) whose options leave
  * tile_items and algorithm automatic.  Candidates: tiles of 4096 or 8192
- * items x the group plan (reads of at most 272 bases) or the LSD plan.  The
+ * items x the group plan (reads of at most 528 bases) or the LSD plan.  The
  * radix digit is 8 bits (the only width built).  scratch_bwt (ceil(N / 16)
  * words) and scratch_dollar_pos (n_reads, may be NULL) receive the BWT;
  * every candidate produces the same one. */

@@ -304,7 +304,7 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   switch (algorithm) {
     case CXBWT_ALGO_LSD: pl.groups = false; break;
     case CXBWT_ALGO_GROUPS:
-      if (!pl.seg_words) return fail(c, CXBWT_EUNSUPPORTED, "the group plan handles reads of at most 272 bases");
+      if (!pl.seg_words) return fail(c, CXBWT_EUNSUPPORTED, "the group plan handles reads of at most 528 bases");
       pl.groups = true;
       break;
     case CXBWT_ALGO_AUTO: pl.groups = pl.seg_words != 0; break;
@@ -415,7 +415,7 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
       return fail(c, CXBWT_EUNSUPPORTED, "collections of mixed read lengths must fit one slice (%llu suffixes, %llu fit)",
                   (unsigned long long)pl.N, (unsigned long long)m1);
     if (!pl.groups)
-      return fail(c, CXBWT_EUNSUPPORTED, "device-memory-bounded slices use the group plan (reads of at most 272 bases)");
+      return fail(c, CXBWT_EUNSUPPORTED, "device-memory-bounded slices use the group plan (reads of at most 528 bases)");
     // Figure 2 step 1: suffixes per bucket; then consecutive buckets packed
     // into slices of at most m1 suffixes.
     CX_TRY(ensure(c, c->bhist, (uint64_t(1) << kBucketBits) * 8, "bucket counts"));

@@ -1,7 +1,7 @@
 // cxbwt_build_batch: many independent collections, few launches, full GPU.
 //
 // Small collections (whose own builds would be bound by launch latency)
-// whose reads all have one length L (at most 272 bases) are packed, in
+// whose reads all have one length L (at most 528 bases) are packed, in
 // order, into "packs" of that length: up to 255 collections and a cap of
 // suffixes per pack.  A pack is built as one collection
 // whose reads are the packs' reads in order (read r of collection c is read

@@ -6,7 +6,13 @@
 
 namespace cxbwt {
 
-constexpr uint32_t kCtaMax = 2048;  // largest group remainder finished by one CTA
+constexpr uint32_t kCtaMax = 2048;  // largest group remainder finished by one CTA (keys of at most 16 words)
+// The CTA finish holds (id, key words, index) per row in shared memory: wide
+// keys (long reads) get fewer rows.
+template <int NW>
+struct CtaRows {
+  static constexpr uint32_t value = NW <= 16 ? kCtaMax : kCtaMax / 2;
+};
 
 struct SegArgs {
   const uint32_t* keys;   // first 16-base window of each row, ascending

@@ -194,7 +194,7 @@ __device__ void finish_long_group(const SegArgs& a, uint32_t gs, uint32_t ge, in
   if (m <= 32) {
     warp_rank_window<NW, V>(a, lo, m, 0u, m, true, lane, sw);
   } else if (lane == 0) {
-    const bool cta = m <= kCtaMax;
+    const bool cta = m <= CtaRows<NW>::value;
     const uint32_t slot = atomicAdd(a.counts + (cta ? 0 : 1), 1u);
     if (slot < (cta ? a.cta_cap : a.big_cap)) (cta ? a.cta_list : a.big_list)[slot] = make_uint2(lo, m);
     else atomicOr(a.err, kErrBounds);
@@ -250,11 +250,12 @@ __global__ void __launch_bounds__(256) k_segsort_warp(const SegArgs a) {
 // Shared-memory bitonic sort of one listed group per CTA (33 .. kCtaMax members).
 template <int NW, class V>
 __global__ void __launch_bounds__(512) k_segsort_cta(const SegArgs a) {
+  constexpr uint32_t kRows = CtaRows<NW>::value;
   extern __shared__ __align__(16) uint32_t sm[];
   V* vals = static_cast<V*>(a.vals);
-  V* s_v = reinterpret_cast<V*>(sm);                                  // [kCtaMax]
-  uint32_t* s_w = reinterpret_cast<uint32_t*>(s_v + kCtaMax);         // [NW][kCtaMax]
-  uint16_t* s_perm = reinterpret_cast<uint16_t*>(s_w + NW * kCtaMax);  // [kCtaMax]
+  V* s_v = reinterpret_cast<V*>(sm);                                // [kRows]
+  uint32_t* s_w = reinterpret_cast<uint32_t*>(s_v + kRows);         // [NW][kRows]
+  uint16_t* s_perm = reinterpret_cast<uint16_t*>(s_w + NW * kRows);  // [kRows]
   __shared__ uint32_t s_item;
   const uint32_t n_list = min(*(volatile uint32_t*)(a.counts + 0), a.cta_cap);
   for (;;) {
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(512) k_segsort_cta(const SegArgs a) {
         uint32_t w[NW];
         gather_words<NW>(a.R, decode(a.R, v), a.depth, w);
 #pragma unroll
-        for (int i = 0; i < NW; ++i) s_w[i * kCtaMax + x] = w[i];
+        for (int i = 0; i < NW; ++i) s_w[i * kRows + x] = w[i];
         s_v[x] = v;
       }
     }
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(512) k_segsort_cta(const SegArgs a) {
               y_less = py < px;
 #pragma unroll
               for (int i = 0; i < NW; ++i) {
-                const uint32_t a0 = s_w[i * kCtaMax + px], b0 = s_w[i * kCtaMax + py];
+                const uint32_t a0 = s_w[i * kRows + px], b0 = s_w[i * kRows + py];
                 if (a0 != b0) {
                   y_less = b0 < a0;
                   break;
@@ -364,7 +365,7 @@ cudaError_t launch_nw(const SegArgs& a, int sm_count, cudaStream_t st) {
   k_segsort_warp<NW, V><<<blocks, 256, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t smem = size_t(kCtaMax) * (sizeof(V) + NW * 4 + 2);
+  const size_t smem = size_t(CtaRows<NW>::value) * (sizeof(V) + NW * 4 + 2);
   static bool configured = false;
   if (!configured) {
     e = cudaFuncSetAttribute(k_segsort_cta<NW, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -385,6 +386,8 @@ cudaError_t launch_v(const SegArgs& a, int nw, int sm_count, cudaStream_t st) {
     case 10: return launch_nw<10, V>(a, sm_count, st);
     case 12: return launch_nw<12, V>(a, sm_count, st);
     case 16: return launch_nw<16, V>(a, sm_count, st);
+    case 24: return launch_nw<24, V>(a, sm_count, st);
+    case 32: return launch_nw<32, V>(a, sm_count, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -401,6 +404,8 @@ int segsort_words(uint32_t max_len) {
   if (nw <= 10) return 10;
   if (nw <= 12) return 12;
   if (nw <= 16) return 16;
+  if (nw <= 24) return 24;
+  if (nw <= 32) return 32;
   return 0;  // reads too long for the on-chip finish
 }
 

@@ -197,7 +197,7 @@ def test_group_plan_rejects_long_reads():
     from paper_1401_7457_gb300 import binding
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    codes, lens = synth.uniform_reads(10, 400, 3)
+    codes, lens = synth.uniform_reads(10, 600, 3)
     with binding.Context(device=0, algorithm=2) as c:
         with pytest.raises(binding.CxbwtError) as e:
             c.build(binding.pack_codes(codes), lens)
@@ -224,3 +224,16 @@ def test_autotune_then_build():
         # same size class, other data
         codes2, lens2 = synth.uniform_reads(12_000, 100, 83)
         assert_same(gpu_bwt(c, codes2, lens2), oracle_of(codes2, lens2))
+
+
+@pytest.mark.parametrize("length,n", [(200, 6000), (400, 3000), (528, 1000)])
+def test_long_reads_group_plan(length, n):
+    """Reads of 200, 400 and 528 bases (the paper's read-length experiment
+    uses 100/200/400 bp): genome-like reads at 30x, group plan vs oracle."""
+    from paper_1401_7457_gb300 import binding
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    g = synth.random_genome(n * length // 30, length)
+    codes, lens = synth.sample_reads(g, n, length, length + 1, 0.01)
+    with binding.Context(device=0, algorithm=2) as c:
+        assert_same(gpu_bwt(c, codes, lens, want_sa=True), oracle_of(codes, lens), sa=True)
