@@ -67,15 +67,19 @@ __device__ __forceinline__ void gather_words(const ReadIndex& R, const Suffix& s
                                                                load_word(R, w0 - o + 4 * c + 3));
     b[4 * c] = x.x; b[4 * c + 1] = x.y; b[4 * c + 2] = x.z; b[4 * c + 3] = x.w;
   }
-  // Word i of the suffix window is store word w0 + i = b[o + i]; pick it
-  // without dynamic register indexing.
+  // Word i of the suffix window is store word w0 + i = b[o + i]: shift the
+  // fetched words down by o in two steps (by 2, then by 1: a logarithmic
+  // shifter, one select per word and step) instead of indexing registers.
+  uint32_t c[NW + 2], d[NW + 1];
+#pragma unroll
+  for (int i = 0; i < NW + 2; ++i) c[i] = (o & 2u) ? b[i + 2] : b[i];
+#pragma unroll
+  for (int i = 0; i < NW + 1; ++i) d[i] = (o & 1u) ? c[i + 1] : c[i];
 #pragma unroll
   for (int i = 0; i < NW; ++i) {
     const uint32_t need = 16u * i;
     if (need < rem) {
-      const uint32_t lo = o == 0 ? b[i] : o == 1 ? b[i + 1] : o == 2 ? b[i + 2] : b[i + 3];
-      const uint32_t hi = o == 0 ? b[i + 1] : o == 1 ? b[i + 2] : o == 2 ? b[i + 3] : b[i + 4];
-      uint32_t x = __funnelshift_l(hi, lo, sh);
+      uint32_t x = __funnelshift_l(d[i + 1], d[i], sh);
       const uint32_t left = rem - need;
       if (left < 16u) x &= ~(0xFFFFFFFFu >> (2u * left));
       w[i] = x;
@@ -83,13 +87,73 @@ __device__ __forceinline__ void gather_words(const ReadIndex& R, const Suffix& s
   }
 }
 
-// (a < b) on (words, position): lexicographic words, then position.
+// Lexicographic comparison as a multiword subtraction: x < y (word 0 most
+// significant) exactly when x - y borrows out of its most significant word.
+// The borrow ripples through the words least significant first, one
+// subtract-with-borrow per word, with no compare-and-select per word.
+// sub_borrow<P> continues a chain over P word pairs given in ascending
+// significance, from a borrow-in b (0 or ~0u), and returns the borrow-out in
+// the same form.  Pairs of equal words (zero padding) pass the borrow on.
+template <int P>
+__device__ __forceinline__ uint32_t sub_borrow(uint32_t b, const uint32_t* x, const uint32_t* y);
+
+template <>
+__device__ __forceinline__ uint32_t sub_borrow<4>(uint32_t b, const uint32_t* x, const uint32_t* y) {
+  uint32_t r;
+  asm("{\n\t.reg .u32 t;\n\t"
+      "sub.cc.u32 t, 0, %1;\n\t"
+      "subc.cc.u32 t, %2, %3;\n\t"
+      "subc.cc.u32 t, %4, %5;\n\t"
+      "subc.cc.u32 t, %6, %7;\n\t"
+      "subc.cc.u32 t, %8, %9;\n\t"
+      "subc.u32 %0, 0, 0;\n\t}"
+      : "=r"(r)
+      : "r"(b), "r"(x[0]), "r"(y[0]), "r"(x[1]), "r"(y[1]), "r"(x[2]), "r"(y[2]), "r"(x[3]), "r"(y[3]));
+  return r;
+}
+
+template <>
+__device__ __forceinline__ uint32_t sub_borrow<8>(uint32_t b, const uint32_t* x, const uint32_t* y) {
+  uint32_t r;
+  asm("{\n\t.reg .u32 t;\n\t"
+      "sub.cc.u32 t, 0, %1;\n\t"
+      "subc.cc.u32 t, %2, %3;\n\t"
+      "subc.cc.u32 t, %4, %5;\n\t"
+      "subc.cc.u32 t, %6, %7;\n\t"
+      "subc.cc.u32 t, %8, %9;\n\t"
+      "subc.cc.u32 t, %10, %11;\n\t"
+      "subc.cc.u32 t, %12, %13;\n\t"
+      "subc.cc.u32 t, %14, %15;\n\t"
+      "subc.cc.u32 t, %16, %17;\n\t"
+      "subc.u32 %0, 0, 0;\n\t}"
+      : "=r"(r)
+      : "r"(b), "r"(x[0]), "r"(y[0]), "r"(x[1]), "r"(y[1]), "r"(x[2]), "r"(y[2]), "r"(x[3]), "r"(y[3]),
+        "r"(x[4]), "r"(y[4]), "r"(x[5]), "r"(y[5]), "r"(x[6]), "r"(y[6]), "r"(x[7]), "r"(y[7]));
+  return r;
+}
+
+// ~0u if (x words, xi) < (y words, yi): words lexicographic (word 0 first),
+// then the row index.  Chains of 8 pairs, the last one of 4 or 8.
 template <int NW>
-__device__ __forceinline__ bool key_less(const uint32_t (&a)[NW], uint32_t pa, const uint32_t (&b)[NW], uint32_t pb) {
+__device__ __forceinline__ uint32_t lex_less_mask(const uint32_t (&x)[NW], uint32_t xi, const uint32_t (&y)[NW],
+                                                  uint32_t yi) {
+  constexpr int P = NW + 1;                        // pairs: the index, then words NW-1 .. 0
+  constexpr int PP = (P % 8 == 0 || P % 8 > 4) ? (P + 7) / 8 * 8 : P / 8 * 8 + 4;
+  uint32_t a[PP], c[PP];
+  a[0] = xi;
+  c[0] = yi;
 #pragma unroll
-  for (int i = 0; i < NW; ++i)
-    if (a[i] != b[i]) return a[i] < b[i];
-  return pa < pb;
+  for (int i = 0; i < NW; ++i) {
+    a[1 + i] = x[NW - 1 - i];
+    c[1 + i] = y[NW - 1 - i];
+  }
+#pragma unroll
+  for (int i = P; i < PP; ++i) a[i] = c[i] = 0u;
+  uint32_t b = 0u;
+#pragma unroll
+  for (int k = 0; k + 8 <= PP; k += 8) b = sub_borrow<8>(b, a + k, c + k);
+  if (PP % 8) b = sub_borrow<4>(b, a + PP / 8 * 8, c + PP / 8 * 8);
+  return b;
 }
 
 template <class V>
@@ -135,24 +199,23 @@ __device__ void warp_rank_window(const SegArgs& a, uint32_t cur, uint32_t n_rows
   __syncwarp();
   const uint32_t gsize = live ? gend - gid : 0u;
   uint32_t rank = 0;
+  uint32_t mine[NW];
+#pragma unroll
+  for (int i = 0; i < NW; ++i) mine[i] = w[i];
   for (uint32_t t = 0; t < gsize; ++t) {
     const uint32_t src = gid + t;
-    // o < w, lexicographic, with the row index breaking ties.
-    bool lt = false, eq = true;
+    // Row src orders before this row: smaller words, or equal words and an
+    // earlier row.  Lanes of one group read one row: a broadcast.
+    uint32_t ov[NW];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      const uint4 o = sw.r[src][q];  // lanes of one group read one row: a broadcast
-      const uint32_t ov[4] = {o.x, o.y, o.z, o.w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        if (4 * q + i < NW) {  // the padding words are zero in every row
-          lt = lt || (eq && ov[i] < w[4 * q + i]);
-          eq = eq && (ov[i] == w[4 * q + i]);
-        }
-      }
+      const uint4 o = sw.r[src][q];
+      if (4 * q < NW) ov[4 * q] = o.x;
+      if (4 * q + 1 < NW) ov[4 * q + 1] = o.y;
+      if (4 * q + 2 < NW) ov[4 * q + 2] = o.z;
+      if (4 * q + 3 < NW) ov[4 * q + 3] = o.w;
     }
-    lt = lt || (eq && src < uint32_t(lane));
-    rank += lt ? 1u : 0u;
+    rank -= lex_less_mask<NW>(ov, src, mine, uint32_t(lane));  // ~0u is -1
   }
   __syncwarp();  // every lane has read its row and the shared words before any overwrite
   if (live && gid + rank != uint32_t(lane)) vals[cur + gid + rank] = v;
