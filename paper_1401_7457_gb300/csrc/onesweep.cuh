@@ -16,13 +16,15 @@
 //   3. rank items inside the tile: warp-level ballots (one per digit bit)
 //      group equal digits; a per-warp shared-memory histogram accumulates
 //      counts in item order, so the ranking is stable,
-//   4. publish the tile's per-digit counts, then walk back over the
-//      predecessors' published counts (decoupled look-back) to find, for each
-//      digit, how many items of earlier tiles precede this tile; the first row
-//      of each digit comes from the all-tile histogram computed before the
-//      pass (digit_base),
-//   5. stage the tile in shared memory in sorted order and write it out, so
-//      that runs of equal digits go to consecutive addresses.
+//   4. publish the tile's per-digit counts, stage the tile in shared memory
+//      in sorted order, and walk back over the predecessors' published counts
+//      (decoupled look-back) to find, for each digit, how many items of
+//      earlier tiles precede this tile (the first look-back load is issued
+//      before the staging, so the two overlap); the first row of each digit
+//      comes from the all-tile histogram computed before the pass
+//      (digit_base),
+//   5. write the staged tile out, so that runs of equal digits go to
+//      consecutive addresses.
 // The only wait is in step 4.  It is bounded by a wall-clock limit; when the
 // limit passes the kernel records kErrTimeout and finishes (it never traps).
 #pragma once
@@ -222,8 +224,9 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
   }
   __syncthreads();
 
-  // ---- 4. tile counts, look-back --------------------------------------------
+  // ---- 4. tile counts; stage sorted while the first look-back load is out --
   uint32_t tile_cnt = 0;
+  unsigned long long prev = 0;  // predecessor's status word, fetched before the staging
   if (tid < kRadix) {
     uint32_t sum = 0;
 #pragma unroll
@@ -243,15 +246,30 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
   if (tid < kRadix) {
 #pragma unroll
     for (int w = 0; w < WARPS; ++w) s_whist[w][tid] += local_excl;
+    if (tile > 0) prev = load_relaxed_u64(a.status + uint64_t(tile - 1) * kRadix + tid);
+  }
+  __syncthreads();
+  // The tile-local sorted order needs only the tile's own counts: write it to
+  // shared memory now, so the staging overlaps the look-back's first load.
+#pragma unroll
+  for (int j = 0; j < IPT; ++j) {
+    const uint32_t d = digit[j] & 0x1FFu;
+    if (d < kRadix) {
+      const uint32_t r = s_whist[warp][d] + (digit[j] >> 9);
+      s_keys[r] = key[j];
+      s_vals[r] = val[j];
+    }
+  }
+  if (tid < kRadix) {
     uint32_t before = 0;  // items with this digit in tiles 0 .. tile-1
     if (tile > 0) {
       const uint32_t agg = 2u * a.epoch, pre = 2u * a.epoch + 1u;
       uint32_t p = tile - 1;
       uint64_t t0 = 0;
       uint32_t spins = 0;
+      unsigned long long st = prev;
       while (true) {
-        const unsigned long long s = load_relaxed_u64(a.status + uint64_t(p) * kRadix + tid);
-        const uint32_t flag = uint32_t(s >> 32);
+        const uint32_t flag = uint32_t(st >> 32);
         if (flag != agg && flag != pre) {  // not yet published in this pass
           ++spins;
           if (spins > 4) __nanosleep(64);
@@ -264,11 +282,13 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
               break;
             }
           }
+          st = load_relaxed_u64(a.status + uint64_t(p) * kRadix + tid);
           continue;
         }
-        before += uint32_t(s);
+        before += uint32_t(st);
         if (flag == pre || p == 0) break;
         --p;
+        st = load_relaxed_u64(a.status + uint64_t(p) * kRadix + tid);
       }
       store_relaxed_u64(a.status + uint64_t(tile) * kRadix + tid,
                         ((unsigned long long)(2u * a.epoch + 1u) << 32) | (before + tile_cnt));
@@ -277,18 +297,8 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
     }
     s_gbase[tid] = __ldg(a.digit_base + tid) + before - local_excl;
   }
-  __syncthreads();
 
-  // ---- 5. stage sorted in shared memory, write out --------------------------
-#pragma unroll
-  for (int j = 0; j < IPT; ++j) {
-    const uint32_t d = digit[j] & 0x1FFu;
-    if (d < kRadix) {
-      const uint32_t r = s_whist[warp][d] + (digit[j] >> 9);
-      s_keys[r] = key[j];
-      s_vals[r] = val[j];
-    }
-  }
+  // ---- 5. write out the staged tile ----------------------------------------
   __syncthreads();
   const uint32_t n_valid = s_kept;
 #pragma unroll
