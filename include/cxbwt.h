@@ -186,6 +186,57 @@ int cxbwt_build_sa(cxbwt_ctx* ctx, const uint32_t* reads_2bit, uint64_t n_reads,
                    uint32_t* out_bwt, uint64_t* out_dollar_pos, uint64_t* out_counts, uint64_t* out_sa,
                    void* stream);
 
+/* ---- bucket-range parts -----------------------------------------------------
+ * Section 3.3 splits the suffixes by their l-prefix into ranges of buckets of
+ * about equal size and builds each range on its own (one per GPU or node);
+ * Section 3.1 builds such ranges one after the other when memory is bounded
+ * (rounds).  B_R is the concatenation of the ranges' parts in bucket order,
+ * because every suffix of a lower bucket sorts before every suffix of a
+ * higher one.  Here a bucket is the first 8 bases of a suffix, A-padded past
+ * the read end (CXBWT_BUCKETS of them).  Parts need reads of one length (at
+ * most 528 bases).  The 8-base buckets are never split: a part holds whole
+ * buckets. */
+#define CXBWT_BUCKETS 65536u
+
+/* Suffixes per bucket (Figure 2 step 1): out_counts (host, CXBWT_BUCKETS
+ * entries) receives the counts; they sum to N.  Synchronous.  EUNSUPPORTED
+ * for reads of mixed lengths. */
+int cxbwt_bucket_counts(cxbwt_ctx* ctx, const uint32_t* reads_2bit, uint64_t n_reads, const uint32_t* lens,
+                        uint64_t* out_counts, void* stream);
+
+/* Host only.  Splits buckets [0, n_buckets) into n_parts consecutive ranges
+ * of about N / n_parts suffixes each: part j is buckets
+ * [bucket_bounds[j], bucket_bounds[j+1]) and rows [row_bounds[j],
+ * row_bounds[j+1]) of B_R (both arrays n_parts + 1 entries, non-decreasing,
+ * from 0 to n_buckets and N).  A part is empty (equal bounds) when there are
+ * more parts than buckets with suffixes.  EINVAL on NULL or n_parts == 0. */
+int cxbwt_split_parts(const uint64_t* counts, uint32_t n_buckets, uint32_t n_parts, uint32_t* bucket_bounds,
+                      uint64_t* row_bounds);
+
+/* Builds the part of B_R made of the suffixes in buckets [bucket_lo,
+ * bucket_hi), 0 <= bucket_lo < bucket_hi <= CXBWT_BUCKETS.  Its rows are
+ * [row0, row0 + rows) of B_R, row0 = the suffixes of the buckets below
+ * bucket_lo (both written to *out_row0 and *out_rows, host, may be NULL).
+ *   out_words       host or device, (row0 % 16 + rows + 15) / 16 words:
+ *                   word j holds global BWT word row0 / 16 + j with only the
+ *                   part's symbols set (the rest of the first and last word
+ *                   is 0), so parts merge by OR (cxbwt_merge_part)
+ *   out_dollar_pos  n_reads entries (may be NULL): as cxbwt_build for reads
+ *                   whose $ row falls in the part, ~0 for the others; the
+ *                   parts' arrays merge by element-wise minimum
+ *   out_counts      5 entries (may be NULL): the part's symbol counts (they
+ *                   add up over the parts)
+ * The caller owns every buffer.  Returns as cxbwt_build; EINVAL for a bad
+ * bucket range, EUNSUPPORTED for mixed read lengths. */
+int cxbwt_build_part(cxbwt_ctx* ctx, const uint32_t* reads_2bit, uint64_t n_reads, const uint32_t* lens,
+                     uint32_t bucket_lo, uint32_t bucket_hi, uint32_t* out_words, uint64_t* out_dollar_pos,
+                     uint64_t* out_counts, uint64_t* out_row0, uint64_t* out_rows, void* stream);
+
+/* Host only.  ORs a part's words (as cxbwt_build_part writes them, rows
+ * [row0, row0 + rows)) into bwt_words, a zero-initialised host buffer of
+ * n_words words of the whole B_R.  EINVAL when the part does not fit. */
+int cxbwt_merge_part(uint32_t* bwt_words, uint64_t n_words, const uint32_t* part_words, uint64_t row0, uint64_t rows);
+
 /* One collection of a batch. */
 typedef struct {
   const uint32_t* reads_2bit;   /* packed bases, host or device (layout above) */

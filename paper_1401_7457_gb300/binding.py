@@ -71,6 +71,11 @@ SIGNATURES = {
     "cxbwt_build_noalloc": (ctypes.c_int, [_VP, _U64, _VP, _VP, _VP, _VP, _VP]),
     "cxbwt_build_batch": (ctypes.c_int, [_VP, _VP, _U64, _VP]),
     "cxbwt_autotune": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP, _VP, _VP, _VP]),
+    "cxbwt_bucket_counts": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP, _VP]),
+    "cxbwt_split_parts": (ctypes.c_int, [_VP, ctypes.c_uint32, ctypes.c_uint32, _VP, _VP]),
+    "cxbwt_build_part": (ctypes.c_int, [_VP, _VP, _U64, _VP, ctypes.c_uint32, ctypes.c_uint32, _VP, _VP, _VP,
+                                        ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), _VP]),
+    "cxbwt_merge_part": (ctypes.c_int, [_VP, _U64, _VP, _U64, _U64]),
     "cxbwt_default_server_options": (None, [_VP]),
     "cxbwt_server_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), _VP]),
     "cxbwt_server_destroy": (None, [_VP]),
@@ -271,6 +276,32 @@ def output_size(lens) -> tuple[int, int]:
     return int(n_sym.value), int(words.value)
 
 
+BUCKETS = 65536  # 8-base buckets of the bucket-range parts
+
+
+def split_parts(counts, n_parts: int) -> tuple[np.ndarray, np.ndarray]:
+    """Bucket and row bounds (n_parts + 1 each) of n_parts ranges of about
+    equal suffix counts (cxbwt_split_parts; host only)."""
+    c = np.ascontiguousarray(_to_numpy(counts), dtype=np.uint64)
+    bb = np.zeros(n_parts + 1, dtype=np.uint32)
+    rb = np.zeros(n_parts + 1, dtype=np.uint64)
+    _check(lib().cxbwt_split_parts(c.ctypes.data, c.size, n_parts, bb.ctypes.data, rb.ctypes.data))
+    return bb, rb
+
+
+def part_words(row0: int, rows: int) -> int:
+    """Words of a part's output (rows [row0, row0 + rows))."""
+    return (row0 % 16 + rows + 15) // 16 if rows else 0
+
+
+def merge_part(bwt_words: np.ndarray, part: np.ndarray, row0: int, rows: int) -> None:
+    """OR a part's words into a zero-initialised host B_R (cxbwt_merge_part)."""
+    assert bwt_words.dtype == np.uint32 and bwt_words.flags.c_contiguous
+    p = np.ascontiguousarray(_to_numpy(part)).view(np.uint32)
+    _check(lib().cxbwt_merge_part(bwt_words.ctypes.data, bwt_words.size, p.ctypes.data if p.size else None,
+                                  row0, rows))
+
+
 def _to_numpy(x):
     if _is_tensor(x):
         return x.detach().cpu().numpy()
@@ -373,6 +404,48 @@ class Context:
                                _ptr(out_counts), st)
         _check(status, self._h)
         return out_bwt, out_dollar_pos, out_counts
+
+    def bucket_counts(self, reads_2bit, lens, stream=None) -> np.ndarray:
+        """Suffixes per 8-base bucket (BUCKETS entries; reads of one length)."""
+        n = int(lens.numel() if _is_tensor(lens) else np.asarray(lens).size)
+        out = np.zeros(BUCKETS, dtype=np.uint64)
+        _check(lib().cxbwt_bucket_counts(self._h, _ptr(reads_2bit), n, _ptr(lens), out.ctypes.data,
+                                         _stream_ptr(stream)), self._h)
+        return out
+
+    def build_part(self, reads_2bit, lens, bucket_lo: int, bucket_hi: int, row0: int, rows: int,
+                   out_words=None, out_dollar_pos=None, out_counts=None, stream=None):
+        """Build the part of B_R of buckets [bucket_lo, bucket_hi), whose rows
+        are [row0, row0 + rows) (from bucket_counts / split_parts).  Missing
+        outputs are allocated on the inputs' side.  Returns
+        ``(words, dollar_pos, counts)``."""
+        n = int(lens.numel() if _is_tensor(lens) else np.asarray(lens).size)
+        nw = max(part_words(row0, rows), 1)
+        if _is_tensor(reads_2bit) and reads_2bit.is_cuda:
+            torch = _torch()
+            dev = reads_2bit.device
+            if out_words is None:
+                out_words = torch.empty(nw, dtype=torch.int32, device=dev)
+            if out_dollar_pos is None:
+                out_dollar_pos = torch.empty(n, dtype=torch.int64, device=dev)
+            if out_counts is None:
+                out_counts = torch.zeros(5, dtype=torch.int64, device=dev)
+        else:
+            if out_words is None:
+                out_words = np.zeros(nw, dtype=np.uint32)
+            if out_dollar_pos is None:
+                out_dollar_pos = np.zeros(n, dtype=np.uint64)
+            if out_counts is None:
+                out_counts = np.zeros(5, dtype=np.uint64)
+        if _nbytes(out_words) < 4 * part_words(row0, rows):
+            raise ValueError("out_words holds fewer words than the part needs")
+        r0, nr = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().cxbwt_build_part(self._h, _ptr(reads_2bit), n, _ptr(lens), bucket_lo, bucket_hi,
+                                      _ptr(out_words), _ptr(out_dollar_pos), _ptr(out_counts), ctypes.byref(r0),
+                                      ctypes.byref(nr), _stream_ptr(stream)), self._h)
+        if (int(r0.value), int(nr.value)) != (row0, rows):
+            raise CxbwtError(-7, f"part rows [{r0.value}, +{nr.value}) differ from the plan's [{row0}, +{rows})")
+        return out_words, out_dollar_pos, out_counts
 
     def build_batch(self, collections, stream=None):
         """collections: list of (reads_2bit, lens, out_bwt, out_dollar_pos, out_counts) arrays/tensors

@@ -227,10 +227,14 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
 }
 
 int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* lens, uint32_t* out_bwt,
-               uint64_t* out_dollar, uint64_t* out_counts, uint64_t* out_sa, void* stream_v) {
+               uint64_t* out_dollar, uint64_t* out_counts, uint64_t* out_sa, void* stream_v, const PartSpec* part) {
   if (!c) return CXBWT_EINVAL;
   c->err.clear();
-  if (!reads || !lens || !out_bwt) return fail(c, CXBWT_EINVAL, "reads_2bit, lens and out_bwt must not be NULL");
+  const bool counts_only = part && part->counts_only;
+  if (!reads || !lens || (!out_bwt && !counts_only))
+    return fail(c, CXBWT_EINVAL, "reads_2bit, lens and out_bwt must not be NULL");
+  if (part && !counts_only && (part->lo >= part->hi || part->hi > (1u << kBucketBits) || out_sa))
+    return fail(c, CXBWT_EINVAL, "a part needs buckets lo < hi <= %u and no suffix array output", 1u << kBucketBits);
   if (n == 0) return fail(c, CXBWT_EINVAL, "n_reads must be at least 1");
   if (n >= (uint64_t(1) << 32)) return fail(c, CXBWT_EUNSUPPORTED, "more than 2^32 - 1 reads in one build");
   CX_CUDA(c, cudaSetDevice(c->device));
@@ -238,7 +242,7 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   c->last_stream = st;
 
   const bool reads_dev = is_device_ptr(reads), lens_dev = is_device_ptr(lens);
-  const bool bwt_dev = is_device_ptr(out_bwt);
+  const bool bwt_dev = out_bwt && is_device_ptr(out_bwt);
   const bool dollar_dev = out_dollar && is_device_ptr(out_dollar);
   const bool counts_dev = out_counts && is_device_ptr(out_counts);
   const bool sa_dev = out_sa && is_device_ptr(out_sa);
@@ -373,19 +377,6 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   r.R = ReadIndex{d_reads, pl.n_words, d_desc, pl.shift, pl.uniform ? pl.Lmax : 0u, uint32_t(n),
                   (reinterpret_cast<uintptr_t>(d_reads) & 15u) == 0 ? 1u : 0u};
 
-  // ---- outputs on the device ---------------------------------------------
-  const uint64_t bwt_words = (pl.N + 15) / 16;
-  r.d_bwt = out_bwt;
-  if (!bwt_dev) {
-    CX_TRY(ensure(c, c->out_bwt, bwt_words * 4, "BWT output"));
-    r.d_bwt = static_cast<uint32_t*>(c->out_bwt.p);
-  }
-  r.d_dollar = out_dollar;
-  if (out_dollar && !dollar_dev) {
-    CX_TRY(ensure(c, c->out_dollar, n * 8, "dollar positions"));
-    r.d_dollar = static_cast<uint64_t*>(c->out_dollar.p);
-  }
-
   // ---- slices --------------------------------------------------------------
   // Device bytes per suffix of a slice: ids and keys (double-buffered),
   // look-back words, group lists; plus the SA staging when it goes to the host.
@@ -400,22 +391,34 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   const uint64_t reusable = c->vals[0].cap + c->vals[1].cap + c->keys[0].cap + c->keys[1].cap + c->status.cap +
                             c->seglist.cap + c->out_sa.cap;
   const uint64_t held_fixed = c->held - reusable;
-  const uint64_t avail = c->budget > held_fixed + fixed ? c->budget - held_fixed - fixed : 0;
+  // Output staging for host buffers is granted below, after the slices are
+  // planned: count what it will add to what is held now (a whole build's size
+  // bounds a part's).
+  uint64_t out_more = 0;
+  if (!bwt_dev && !counts_only) {
+    const uint64_t need = ((pl.N + 15) / 16 + 1) * 4;
+    out_more += need > c->out_bwt.cap ? need - c->out_bwt.cap + (2u << 20) : 0;
+  }
+  if (out_dollar && !dollar_dev) out_more += n * 8 > c->out_dollar.cap ? n * 8 - c->out_dollar.cap + (2u << 20) : 0;
+  const uint64_t avail =
+      c->budget > held_fixed + fixed + out_more ? c->budget - held_fixed - fixed - out_more : 0;
   uint64_t m1 = uint64_t(double(avail) / per_row);
   // A slice must fit 32-bit row counts; every workspace buffer below is
   // granted in 2 MB steps, so leave room for that rounding.
   m1 = std::min<uint64_t>(m1 > (64u << 20) ? m1 - (1u << 20) : (m1 > 32768 ? m1 - 16384 : m1), 0xFFFFFFF0ull);
   std::vector<Slice> slices;
-  if (pl.N <= m1) {
+  uint64_t part_row0 = 0, part_rows = pl.N;  // global rows this call emits
+  if (pl.N <= m1 && !part) {
     Slice sl;
     sl.rows = uint32_t(pl.N);
     slices.push_back(sl);
   } else {
     if (!pl.uniform)
-      return fail(c, CXBWT_EUNSUPPORTED, "collections of mixed read lengths must fit one slice (%llu suffixes, %llu fit)",
+      return fail(c, CXBWT_EUNSUPPORTED, part ? "bucket-range parts need reads of one length"
+                                              : "collections of mixed read lengths must fit one slice (%llu suffixes, %llu fit)",
                   (unsigned long long)pl.N, (unsigned long long)m1);
     if (!pl.groups)
-      return fail(c, CXBWT_EUNSUPPORTED, "device-memory-bounded slices use the group plan (reads of at most 528 bases)");
+      return fail(c, CXBWT_EUNSUPPORTED, "device-memory-bounded slices and parts use the group plan (reads of at most 528 bases)");
     // Figure 2 step 1: suffixes per bucket; then consecutive buckets packed
     // into slices of at most m1 suffixes.
     CX_TRY(ensure(c, c->bhist, (uint64_t(1) << kBucketBits) * 8, "bucket counts"));
@@ -427,10 +430,17 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
     CX_CUDA(c, cudaMemcpyAsync(bh.data(), c->bhist.p, bh.size() * 8, cudaMemcpyDeviceToHost, st));
     CX_CUDA(c, cudaStreamSynchronize(st));
     r.d2h += bh.size() * 8;
+    if (counts_only) {
+      std::memcpy(part->bucket_counts, bh.data(), bh.size() * 8);
+      return CXBWT_OK;
+    }
+    const uint32_t b_lo = part ? part->lo : 0u, b_hi = part ? part->hi : uint32_t(bh.size());
     uint64_t row = 0, acc = 0;
-    uint32_t lo = 0;
-    for (uint32_t b = 0; b <= bh.size(); ++b) {
-      const bool end = (b == bh.size());
+    for (uint32_t b = 0; b < b_lo; ++b) row += bh[b];
+    part_row0 = row;
+    uint32_t lo = b_lo;
+    for (uint32_t b = b_lo; b <= b_hi; ++b) {
+      const bool end = (b == b_hi);
       const uint64_t cnt = end ? 0 : bh[b];
       if (!end && cnt > m1)
         return fail(c, CXBWT_ENOMEM, "one 8-base bucket holds %llu suffixes, more than the %llu a slice can hold",
@@ -451,11 +461,45 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
       }
       acc += cnt;
     }
-    if (row != pl.N) return fail(c, CXBWT_EINTERNAL, "bucket counts sum to %llu, not N", (unsigned long long)row);
+    part_rows = row - part_row0;
+    if (!part) {
+      if (row != pl.N) return fail(c, CXBWT_EINTERNAL, "bucket counts sum to %llu, not N", (unsigned long long)row);
+    } else {
+      uint64_t total = row;
+      for (uint32_t b = b_hi; b < bh.size(); ++b) total += bh[b];
+      if (total != pl.N) return fail(c, CXBWT_EINTERNAL, "bucket counts sum to %llu, not N", (unsigned long long)total);
+    }
     // Gathers walk the store in address order when it is too big for L2.
     r.read_major = pl.Lmax <= 255 && (pl.n_words * 4 > (64u << 20) || (c->opt.plan_flags & CXBWT_PLAN_READ_MAJOR));
+  }
+  if (part) {
+    if (part->row0) *part->row0 = part_row0;
+    if (part->rows) *part->rows = part_rows;
+  }
+
+  // ---- outputs on the device ---------------------------------------------
+  // The output holds global words [word0, word0 + bwt_words): all of them for
+  // a whole build, those the part's rows touch for a part.
+  const uint64_t word0 = part_row0 / 16;
+  const uint64_t bwt_words = (part_row0 + part_rows + 15) / 16 - word0;
+  r.d_bwt = out_bwt;
+  if (!bwt_dev) {
+    CX_TRY(ensure(c, c->out_bwt, bwt_words * 4, "BWT output"));
+    r.d_bwt = static_cast<uint32_t*>(c->out_bwt.p);
+  }
+  r.d_dollar = out_dollar;
+  if (out_dollar && !dollar_dev) {
+    CX_TRY(ensure(c, c->out_dollar, n * 8, "dollar positions"));
+    r.d_dollar = static_cast<uint64_t*>(c->out_dollar.p);
+  }
+
+  if (slices.size() > 1 || part) {
     CX_CUDA(c, cudaMemsetAsync(r.d_bwt, 0, bwt_words * 4, st));  // slice edges are merged with atomicOr
   }
+  if (part && r.d_dollar) {
+    CX_CUDA(c, cudaMemsetAsync(r.d_dollar, 0xFF, n * 8, st));  // reads whose $ row is in another part
+  }
+
   uint32_t max_rows = 0;
   for (const Slice& sl : slices) max_rows = std::max(max_rows, sl.rows);
   const uint64_t gen_tiles = (pl.N + TILE - 1) / TILE;
@@ -526,7 +570,7 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
     e.n_total = pl.N;
     e.R = r.R;
     e.bwt = r.d_bwt;
-    e.word_base = 0;
+    e.word_base = word0;
     e.dollar_pos = r.d_dollar;
     e.counts = r.d_counts;
     e.sa_out = r.d_sa ? (sa_dev ? r.d_sa + sl.row0 : r.d_sa) : nullptr;
@@ -544,7 +588,7 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
     if (!bwt_dev) {
       // Words whose 16 rows are all emitted stream to the host while the next slice sorts.
       const bool last = si + 1 == slices.size();
-      const uint64_t done = last ? bwt_words : (sl.row0 + sl.rows) / 16;
+      const uint64_t done = last ? bwt_words : (sl.row0 + sl.rows) / 16 - word0;
       if (done > words_sent) {
         cudaEvent_t ev = c->slice_done[si & 1];
         CX_CUDA(c, cudaEventRecord(ev, st));
@@ -618,6 +662,59 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
 extern "C" {
 
 int cxbwt_abi_version(void) { return CXBWT_ABI_VERSION; }
+
+int cxbwt_bucket_counts(cxbwt_ctx* ctx, const uint32_t* reads_2bit, uint64_t n_reads, const uint32_t* lens,
+                        uint64_t* out_counts, void* stream) {
+  if (!ctx) return CXBWT_EINVAL;
+  if (!out_counts) return fail(ctx, CXBWT_EINVAL, "out_counts must not be NULL");
+  PartSpec p;
+  p.counts_only = true;
+  p.bucket_counts = out_counts;
+  return build_impl(ctx, reads_2bit, n_reads, lens, nullptr, nullptr, nullptr, nullptr, stream, &p);
+}
+
+int cxbwt_split_parts(const uint64_t* counts, uint32_t n_buckets, uint32_t n_parts, uint32_t* bucket_bounds,
+                      uint64_t* row_bounds) {
+  if (!counts || !bucket_bounds || !row_bounds || n_parts == 0) return CXBWT_EINVAL;
+  uint64_t total = 0;
+  for (uint32_t b = 0; b < n_buckets; ++b) total += counts[b];
+  // Boundary j goes where the running count comes closest to j * N / n_parts.
+  uint32_t b = 0;
+  uint64_t below = 0;  // suffixes in buckets [0, b)
+  bucket_bounds[0] = 0;
+  row_bounds[0] = 0;
+  for (uint32_t j = 1; j < n_parts; ++j) {
+    const uint64_t target = uint64_t((unsigned __int128)total * j / n_parts);
+    while (b < n_buckets && below + counts[b] <= target) below += counts[b++];
+    // Take bucket b too when that lands closer to the target.
+    if (b < n_buckets && below < target && below + counts[b] - target < target - below) below += counts[b++];
+    bucket_bounds[j] = b;
+    row_bounds[j] = below;
+  }
+  bucket_bounds[n_parts] = n_buckets;
+  row_bounds[n_parts] = total;
+  return CXBWT_OK;
+}
+
+int cxbwt_build_part(cxbwt_ctx* ctx, const uint32_t* reads_2bit, uint64_t n_reads, const uint32_t* lens,
+                     uint32_t bucket_lo, uint32_t bucket_hi, uint32_t* out_words, uint64_t* out_dollar_pos,
+                     uint64_t* out_counts, uint64_t* out_row0, uint64_t* out_rows, void* stream) {
+  PartSpec p;
+  p.lo = bucket_lo;
+  p.hi = bucket_hi;
+  p.row0 = out_row0;
+  p.rows = out_rows;
+  return build_impl(ctx, reads_2bit, n_reads, lens, out_words, out_dollar_pos, out_counts, nullptr, stream, &p);
+}
+
+int cxbwt_merge_part(uint32_t* bwt_words, uint64_t n_words, const uint32_t* part_words, uint64_t row0, uint64_t rows) {
+  if (!bwt_words || (!part_words && rows)) return CXBWT_EINVAL;
+  if (rows == 0) return CXBWT_OK;
+  const uint64_t w0 = row0 / 16, w1 = (row0 + rows + 15) / 16;
+  if (row0 + rows < row0 || w1 > n_words) return CXBWT_EINVAL;
+  for (uint64_t w = w0; w < w1; ++w) bwt_words[w] |= part_words[w - w0];
+  return CXBWT_OK;
+}
 
 void cxbwt_default_options(cxbwt_options* opt) {
   if (!opt) return;

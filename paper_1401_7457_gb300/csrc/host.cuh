@@ -163,6 +163,18 @@ struct Slice {
   uint64_t row0 = 0;          // global BWT row of its first suffix
 };
 
+// A bucket-range part of a build (Section 3.3): only the suffixes whose first
+// 8 bases (A-padded) fall in buckets [lo, hi) are sorted and emitted, into an
+// output that starts at the part's first global word.  counts_only: return
+// the per-bucket suffix counts (Figure 2 step 1) and build nothing.
+struct PartSpec {
+  uint32_t lo = 0, hi = 0;
+  bool counts_only = false;
+  uint64_t* bucket_counts = nullptr;  // host, 2^kBucketBits entries (counts_only)
+  uint64_t* row0 = nullptr;           // host: the part's first global row
+  uint64_t* rows = nullptr;           // host: its number of rows
+};
+
 // Per-build device state shared by the slices.
 struct Run {
   cudaStream_t st = nullptr;
@@ -221,7 +233,8 @@ inline bool tuned_choice(const cxbwt_ctx* c, uint32_t max_len, uint64_t n_suffix
 int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t* tev);
 // One whole build (api.cu).
 int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* lens, uint32_t* out_bwt,
-               uint64_t* out_dollar, uint64_t* out_counts, uint64_t* out_sa, void* stream_v);
+               uint64_t* out_dollar, uint64_t* out_counts, uint64_t* out_sa, void* stream_v,
+               const PartSpec* part = nullptr);
 
 }  // namespace host
 }  // namespace cxbwt
