@@ -425,6 +425,75 @@ def run_length_bench(args, rank, world):
     return 0
 
 
+def _timed(fn, steps, flush):
+    """Mean CUDA-event time of fn() over steps calls, L2 flushed before each."""
+    import torch
+    ts = []
+    for _ in range(steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return sum(ts) / len(ts)
+
+
+def run_parts_bench(args, rank, world):
+    """Bucket-range parts of the genome-like collection (Section 3.3's
+    partition, built one after another on this GPU): per-part device time for
+    2, 4 and 8 parts against the whole build, and the checkpointed rounds
+    (Section 3.1) end to end into files.  One JSON line (not the benchmark's
+    default line)."""
+    import tempfile
+
+    import torch
+
+    from paper_1401_7457_gb300 import binding, build, parts
+    build.build()
+    dev = torch.device("cuda", 0)
+    _, codes, lens = load_workload("genome-like", 0, args.reads)
+    bases = int(lens.sum())
+    w = torch.from_numpy(binding.pack_codes(codes).view(np.int32)).to(dev)
+    ln = torch.from_numpy(lens.view(np.int32)).to(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    ctx = binding.Context(device=0)
+    outs = ctx.build(w, ln)
+    whole_ms = _timed(lambda: ctx.build(w, ln, *outs), args.steps, flush)
+    counts = ctx.bucket_counts(w, ln)
+    res = {"whole_ms": whole_ms}
+    for P in (2, 4, 8):
+        plan = parts.plan_parts(counts, P)
+        per = []
+        for p in plan:
+            o = ctx.build_part(w, ln, p.lo, p.hi, p.row0, p.rows)
+            for _ in range(max(args.warmup, 1)):
+                ctx.build_part(w, ln, p.lo, p.hi, p.row0, p.rows, *o)
+            per.append(_timed(lambda: ctx.build_part(w, ln, p.lo, p.hi, p.row0, p.rows, *o), args.steps, flush))
+        res[f"{P}_parts"] = {"part_ms": per, "sum_ms": sum(per), "max_ms": max(per),
+                             "rows": [p.rows for p in plan]}
+    with tempfile.TemporaryDirectory() as tmp:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = parts.build_rounds(ctx, w, ln, 4, tmp)
+        rounds_s = time.perf_counter() - t0
+        assert st["done"]
+        ref = outs[0].cpu().numpy().view(np.uint32)
+        same = bool(np.array_equal(np.fromfile(f"{tmp}/bwt.u32", dtype=np.uint32), ref))
+    res["rounds_4_to_files"] = {"s": rounds_s, "gbase_per_s": bases / rounds_s / 1e9, "equal_to_whole_build": same}
+    ctx.close()
+    line = {"metric": METRIC, "value": bases / (whole_ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": whole_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "bucket-range parts of the genome-like collection (1M x 100 bp)",
+                       "l2": "flushed between steps"},
+            "parts": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -435,7 +504,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reads", type=int, default=0,
                     help="reads per GPU (0: the workload's own size; smaller only for profiling captures)")
-    ap.add_argument("--workload", default="genome-like", choices=sorted(WORKLOADS) + ["batch", "serve", "length"],
+    ap.add_argument("--workload", default="genome-like", choices=sorted(WORKLOADS) + ["batch", "serve", "length", "parts"],
                     help="genome-like is the benchmark; the others are parity-test workloads timed for reference")
     ap.add_argument("--budget-gb", type=float, default=0.0,
                     help="device budget of the library context (0: 90%% of free memory)")
@@ -449,6 +518,8 @@ def main():
         return run_serve_bench(args, rank, world)
     if args.workload == "length":
         return run_length_bench(args, rank, world)
+    if args.workload == "parts":
+        return run_parts_bench(args, rank, world)
 
     import torch
     import torch.distributed as dist
