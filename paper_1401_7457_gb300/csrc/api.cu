@@ -236,7 +236,8 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   if (part && !counts_only && (part->lo >= part->hi || part->hi > (1u << kBucketBits) || out_sa))
     return fail(c, CXBWT_EINVAL, "a part needs buckets lo < hi <= %u and no suffix array output", 1u << kBucketBits);
   if (n == 0) return fail(c, CXBWT_EINVAL, "n_reads must be at least 1");
-  if (n >= (uint64_t(1) << 32)) return fail(c, CXBWT_EUNSUPPORTED, "more than 2^32 - 1 reads in one build");
+  // (the generated start order steps read indices by 32 in 32 bits)
+  if (n > (uint64_t(1) << 32) - 64) return fail(c, CXBWT_EUNSUPPORTED, "more than 2^32 - 64 reads in one build");
   CX_CUDA(c, cudaSetDevice(c->device));
   cudaStream_t st = static_cast<cudaStream_t>(stream_v);
   c->last_stream = st;

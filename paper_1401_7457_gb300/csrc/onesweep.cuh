@@ -97,228 +97,228 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
   const I warp_base = tile_base + I(warp) * 32u * IPT + lane;
   const I n_in = I(a.n_gen);
 
-  uint32_t key[IPT], digit[IPT];
-  V val[IPT];
+  // A tile with a dropped row (the last one, or any when filtering) ranks a
+  // 9th digit bit and checks rows against the input's end; every other tile
+  // skips both.
+  auto tile_body = [&](auto ninth_c) {
+    constexpr bool NINTH = decltype(ninth_c)::value;
+    uint32_t key[IPT], digit[IPT];
+    V val[IPT];
 
-  // ---- 2. load ------------------------------------------------------------
-  if (MODE == kSrcInitUniform) {
-    const uint32_t L = a.R.uniform_len;
-    if (a.n_gen <= 0xFFFFFFFFull) {  // 32-bit division while the enumeration fits
-#pragma unroll
+    // ---- 2. load ------------------------------------------------------------
+    if (MODE == kSrcInitUniform) {
+      // Row idx of the (suffix length, read) order: length idx / n, read
+      // idx % n.  One division per thread; its next rows (idx + 32, ...) step
+      // the remainder and carry into the quotient.
+      const uint32_t L = a.R.uniform_len, n = a.n_reads;
+      const I slen0 = warp_base / n;
+      uint32_t slen = uint32_t(min(slen0, I(L + 1)));
+      uint32_t i = uint32_t(warp_base - slen0 * n);
+  #pragma unroll
       for (int j = 0; j < IPT; ++j) {
-        const uint32_t idx = uint32_t(warp_base) + j * 32;
-        // Row idx of the (suffix length, read) order: length idx / n, read idx % n.
-        const uint32_t slen = idx / a.n_reads;
-        const uint32_t i = idx - slen * a.n_reads;
         val[j] = (V(i) << a.R.shift) | V(L - min(slen, L));
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < IPT; ++j) {
-        const I idx = warp_base + j * 32;
-        const I slen = idx / a.n_reads;
-        const uint32_t i = uint32_t(idx - slen * a.n_reads);
-        val[j] = (V(i) << a.R.shift) | V(L - uint32_t(min(slen, I(L))));
-      }
-    }
-  } else if (MODE == kSrcInitReadMajor) {
-    const uint32_t L1 = a.R.uniform_len + 1;
-    if (a.n_gen <= 0xFFFFFFFFull) {
-#pragma unroll
-      for (int j = 0; j < IPT; ++j) {
-        const uint32_t idx = uint32_t(warp_base) + j * 32;
-        // Row idx of the read-major order: read idx / (L+1), offset idx % (L+1).
-        const uint32_t i = idx / L1;
-        val[j] = (V(i) << a.R.shift) | V(idx - i * L1);
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < IPT; ++j) {
-        const I idx = warp_base + j * 32;
-        const I i = idx / L1;
-        val[j] = (V(i) << a.R.shift) | V(uint32_t(idx - i * L1));
-      }
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-      const I idx = warp_base + j * 32;
-      val[j] = idx < n_in ? __ldg(vals_in + idx) : V(0);
-    }
-  }
-  if (MODE == kSrcCarried) {
-#pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-      const I idx = warp_base + j * 32;
-      key[j] = idx < n_in ? __ldg(a.keys_in + idx) : 0u;
-    }
-  } else if (MODE == kSrcLength) {
-#pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-      const Suffix s = decode(a.R, val[j]);
-      key[j] = s.len - s.k;
-    }
-  } else if (MODE == kSrcCollection) {
-#pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-      // Collection of the id's read: the last c with s_coll[c] <= read.
-      const uint32_t read = uint32_t(val[j] >> a.R.shift);
-      uint32_t lo = 0, hi = a.n_coll;
-      while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (s_coll[mid] <= read) lo = mid; else hi = mid;
-      }
-      key[j] = lo;
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-      const I idx = warp_base + j * 32;
-      key[j] = idx < n_in ? window16(a.R, decode(a.R, val[j]), a.window_c0) : 0u;
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < IPT; ++j) {
-    const I idx = warp_base + j * 32;
-    bool keep = idx < n_in;
-    if (FILTER) keep = keep && ((key[j] >> a.bucket_shift) - a.bucket_lo) < (a.bucket_hi - a.bucket_lo);
-    uint32_t d;
-    if (LEN_DIGIT) d = a.R.uniform_len - (uint32_t(val[j]) & ((1u << a.R.shift) - 1u));
-    else d = (key[j] >> a.key_shift) & (kRadix - 1);
-    // Rows past the end (or filtered out) get a value no digit has, so they
-    // match only each other and are neither counted nor written.
-    digit[j] = keep ? d : uint32_t(kRadix);
-  }
-
-  // ---- 3. stable rank inside the warp, in item order ------------------------
-  // Lanes holding the same digit are found with one ballot per digit bit (a
-  // 9th bit separates dropped rows: only in the last tile unless filtering):
-  // cheaper on sm_103a than __match_any_sync.  digit[j] becomes
-  // (rank of the item among the warp's items of its digit) << 9 | digit.
-  const uint32_t lt = lanemask_lt();
-  const bool ninth = FILTER || (tile == a.n_tiles - 1);
-#pragma unroll
-  for (int j = 0; j < IPT; ++j) {
-    const uint32_t d = digit[j];
-    uint32_t peers = 0xFFFFFFFFu;
-#pragma unroll
-    for (int b = 0; b < kRadixBits; ++b) {
-      const uint32_t bit = (d >> b) & 1u;
-      const uint32_t m = __ballot_sync(0xFFFFFFFFu, bit);
-      peers &= bit ? m : ~m;
-    }
-    if (ninth) {
-      const uint32_t bit = d >> kRadixBits;
-      const uint32_t m = __ballot_sync(0xFFFFFFFFu, bit);
-      peers &= bit ? m : ~m;
-    }
-    const int leader = __ffs(peers) - 1;
-    uint32_t prior = 0;
-    if (lane == leader && d < kRadix) {
-      prior = s_whist[warp][d];
-      s_whist[warp][d] = prior + __popc(peers);
-    }
-    prior = __shfl_sync(0xFFFFFFFFu, prior, leader);
-    digit[j] = ((prior + __popc(peers & lt)) << 9) | d;
-    __syncwarp();
-  }
-  __syncthreads();
-
-  // ---- 4. tile counts; stage sorted while the first look-back load is out --
-  uint32_t tile_cnt = 0;
-  unsigned long long prev = 0;  // predecessor's status word, fetched before the staging
-  if (tid < kRadix) {
-    uint32_t sum = 0;
-#pragma unroll
-    for (int w = 0; w < WARPS; ++w) {
-      const uint32_t c = s_whist[w][tid];
-      s_whist[w][tid] = sum;
-      sum += c;
-    }
-    tile_cnt = sum;
-    const unsigned long long agg_flag = (unsigned long long)(2u * a.epoch) << 32;
-    const unsigned long long pre_flag = (unsigned long long)(2u * a.epoch + 1u) << 32;
-    if (!(tile == 0 && a.stall_tile0))
-      store_relaxed_u64(a.status + uint64_t(tile) * kRadix + tid, (tile == 0 ? pre_flag : agg_flag) | tile_cnt);
-  }
-  const uint32_t local_excl = block_exclusive_scan_256<THREADS>(tile_cnt, s_scan);
-  if (tid == kRadix - 1) s_kept = local_excl + tile_cnt;  // rows of this tile that are written
-  if (tid < kRadix) {
-#pragma unroll
-    for (int w = 0; w < WARPS; ++w) s_whist[w][tid] += local_excl;
-    if (tile > 0) prev = load_relaxed_u64(a.status + uint64_t(tile - 1) * kRadix + tid);
-  }
-  __syncthreads();
-  // The tile-local sorted order needs only the tile's own counts: write it to
-  // shared memory now, so the staging overlaps the look-back's first load.
-#pragma unroll
-  for (int j = 0; j < IPT; ++j) {
-    const uint32_t d = digit[j] & 0x1FFu;
-    if (d < kRadix) {
-      const uint32_t r = s_whist[warp][d] + (digit[j] >> 9);
-      s_keys[r] = key[j];
-      s_vals[r] = val[j];
-    }
-  }
-  if (tid < kRadix) {
-    uint32_t before = 0;  // items with this digit in tiles 0 .. tile-1
-    if (tile > 0) {
-      const uint32_t agg = 2u * a.epoch, pre = 2u * a.epoch + 1u;
-      uint32_t p = tile - 1;
-      uint64_t t0 = 0;
-      uint32_t spins = 0;
-      unsigned long long st = prev;
-      while (true) {
-        const uint32_t flag = uint32_t(st >> 32);
-        if (flag != agg && flag != pre) {  // not yet published in this pass
-          ++spins;
-          if (spins > 4) __nanosleep(64);
-          if ((spins & 63u) == 0u) {
-            const uint64_t now = global_timer_ns();
-            if (t0 == 0) {
-              t0 = now;
-            } else if (now - t0 > a.timeout_ns) {
-              atomicOr(a.err, kErrTimeout);
-              break;
-            }
-          }
-          st = load_relaxed_u64(a.status + uint64_t(p) * kRadix + tid);
-          continue;
+        i += 32;
+        while (i >= n) {  // once per step when n >= 32
+          i -= n;
+          slen = min(slen + 1, L + 1);
         }
-        before += uint32_t(st);
-        if (flag == pre || p == 0) break;
-        --p;
-        st = load_relaxed_u64(a.status + uint64_t(p) * kRadix + tid);
       }
-      store_relaxed_u64(a.status + uint64_t(tile) * kRadix + tid,
-                        ((unsigned long long)(2u * a.epoch + 1u) << 32) | (before + tile_cnt));
-      // (after a wait that ran out, `before` is short: the outputs are then
-      // unspecified but every write stays in bounds, and the error word says so)
+    } else if (MODE == kSrcInitReadMajor) {
+      // Row idx of the read-major order: read idx / (L+1), offset idx % (L+1),
+      // stepped the same way.
+      const uint32_t L1 = a.R.uniform_len + 1;
+      const I i0 = warp_base / L1;
+      uint32_t k = uint32_t(warp_base - i0 * L1);
+      V i = V(i0);
+  #pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        val[j] = (i << a.R.shift) | V(k);
+        k += 32;
+        while (k >= L1) {
+          k -= L1;
+          ++i;
+        }
+      }
+    } else {
+  #pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        const I idx = warp_base + j * 32;
+        val[j] = (!NINTH || idx < n_in) ? __ldg(vals_in + idx) : V(0);
+      }
     }
-    s_gbase[tid] = __ldg(a.digit_base + tid) + before - local_excl;
-  }
-
-  // ---- 5. write out the staged tile ----------------------------------------
-  __syncthreads();
-  const uint32_t n_valid = s_kept;
-#pragma unroll
-  for (int j = 0; j < IPT; ++j) {
-    const uint32_t r = j * THREADS + tid;
-    if (r < n_valid) {
-      const uint32_t k = s_keys[r];
-      const V v = s_vals[r];
+    if (MODE == kSrcCarried) {
+  #pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        const I idx = warp_base + j * 32;
+        key[j] = (!NINTH || idx < n_in) ? __ldg(a.keys_in + idx) : 0u;
+      }
+    } else if (MODE == kSrcLength) {
+  #pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        const Suffix s = decode(a.R, val[j]);
+        key[j] = s.len - s.k;
+      }
+    } else if (MODE == kSrcCollection) {
+  #pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        // Collection of the id's read: the last c with s_coll[c] <= read.
+        const uint32_t read = uint32_t(val[j] >> a.R.shift);
+        uint32_t lo = 0, hi = a.n_coll;
+        while (hi - lo > 1) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (s_coll[mid] <= read) lo = mid; else hi = mid;
+        }
+        key[j] = lo;
+      }
+    } else {
+  #pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        const I idx = warp_base + j * 32;
+        key[j] = (!NINTH || idx < n_in) ? window16(a.R, decode(a.R, val[j]), a.window_c0) : 0u;
+      }
+    }
+  #pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const I idx = warp_base + j * 32;
+      bool keep = !NINTH || idx < n_in;
+      if (FILTER) keep = keep && ((key[j] >> a.bucket_shift) - a.bucket_lo) < (a.bucket_hi - a.bucket_lo);
       uint32_t d;
-      if (LEN_DIGIT) d = a.R.uniform_len - (uint32_t(v) & ((1u << a.R.shift) - 1u));
-      else d = (k >> a.key_shift) & (kRadix - 1);
-      const uint32_t g = s_gbase[d] + r;
-      if (g < a.n_out) {
-        vals_out[g] = v;
-        if (WRITE_KEY) a.keys_out[g] = k;
-      } else {
-        atomicOr(a.err, kErrBounds);  // digit bases disagree with the items: never write out of bounds
+      if (LEN_DIGIT) d = a.R.uniform_len - (uint32_t(val[j]) & ((1u << a.R.shift) - 1u));
+      else d = (key[j] >> a.key_shift) & (kRadix - 1);
+      // Rows past the end (or filtered out) get a value no digit has, so they
+      // match only each other and are neither counted nor written.
+      digit[j] = keep ? d : uint32_t(kRadix);
+    }
+
+    // ---- 3. stable rank inside the warp, in item order ------------------------
+    // Lanes holding the same digit are found with one ballot per digit bit (a
+    // 9th bit separates dropped rows: only in the last tile unless filtering):
+    // cheaper on sm_103a than __match_any_sync.  Every lane reads its digit's
+    // running count; the lowest lane of each digit adds the group's size.
+    // digit[j] becomes (rank of the item among the warp's items of its digit)
+    // << 9 | digit.
+    const uint32_t lt = lanemask_lt();
+  #pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const uint32_t d = digit[j];
+      uint32_t peers = 0xFFFFFFFFu;
+  #pragma unroll
+      for (int b = 0; b < kRadixBits; ++b) {
+        const uint32_t bit = (d >> b) & 1u;
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, bit);
+        peers &= bit ? m : ~m;
+      }
+      if (NINTH) {
+        const uint32_t bit = d >> kRadixBits;
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, bit);
+        peers &= bit ? m : ~m;
+      }
+      const uint32_t prior = s_whist[warp][d & (kRadix - 1)];  // dropped rows read a count they never use
+      if ((peers & lt) == 0 && (!NINTH || d < kRadix)) s_whist[warp][d] = prior + __popc(peers);
+      digit[j] = ((prior + __popc(peers & lt)) << 9) | d;
+      __syncwarp();
+    }
+    __syncthreads();
+
+    // ---- 4. tile counts; stage sorted while the first look-back load is out --
+    uint32_t tile_cnt = 0;
+    unsigned long long prev = 0;  // predecessor's status word, fetched before the staging
+    if (tid < kRadix) {
+      uint32_t sum = 0;
+  #pragma unroll
+      for (int w = 0; w < WARPS; ++w) {
+        const uint32_t c = s_whist[w][tid];
+        s_whist[w][tid] = sum;
+        sum += c;
+      }
+      tile_cnt = sum;
+      const unsigned long long agg_flag = (unsigned long long)(2u * a.epoch) << 32;
+      const unsigned long long pre_flag = (unsigned long long)(2u * a.epoch + 1u) << 32;
+      if (!(tile == 0 && a.stall_tile0))
+        store_relaxed_u64(a.status + uint64_t(tile) * kRadix + tid, (tile == 0 ? pre_flag : agg_flag) | tile_cnt);
+    }
+    const uint32_t local_excl = block_exclusive_scan_256<THREADS>(tile_cnt, s_scan);
+    if (tid == kRadix - 1) s_kept = local_excl + tile_cnt;  // rows of this tile that are written
+    if (tid < kRadix) {
+  #pragma unroll
+      for (int w = 0; w < WARPS; ++w) s_whist[w][tid] += local_excl;
+      if (tile > 0) prev = load_relaxed_u64(a.status + uint64_t(tile - 1) * kRadix + tid);
+    }
+    __syncthreads();
+    // The tile-local sorted order needs only the tile's own counts: write it to
+    // shared memory now, so the staging overlaps the look-back's first load.
+  #pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const uint32_t d = digit[j] & 0x1FFu;
+      if (!NINTH || d < kRadix) {
+        const uint32_t r = s_whist[warp][d] + (digit[j] >> 9);
+        s_keys[r] = key[j];
+        s_vals[r] = val[j];
       }
     }
-  }
+    if (tid < kRadix) {
+      uint32_t before = 0;  // items with this digit in tiles 0 .. tile-1
+      if (tile > 0) {
+        const uint32_t agg = 2u * a.epoch, pre = 2u * a.epoch + 1u;
+        uint32_t p = tile - 1;
+        uint64_t t0 = 0;
+        uint32_t spins = 0;
+        unsigned long long st = prev;
+        while (true) {
+          const uint32_t flag = uint32_t(st >> 32);
+          if (flag != agg && flag != pre) {  // not yet published in this pass
+            ++spins;
+            if (spins > 4) __nanosleep(64);
+            if ((spins & 63u) == 0u) {
+              const uint64_t now = global_timer_ns();
+              if (t0 == 0) {
+                t0 = now;
+              } else if (now - t0 > a.timeout_ns) {
+                atomicOr(a.err, kErrTimeout);
+                break;
+              }
+            }
+            st = load_relaxed_u64(a.status + uint64_t(p) * kRadix + tid);
+            continue;
+          }
+          before += uint32_t(st);
+          if (flag == pre || p == 0) break;
+          --p;
+          st = load_relaxed_u64(a.status + uint64_t(p) * kRadix + tid);
+        }
+        store_relaxed_u64(a.status + uint64_t(tile) * kRadix + tid,
+                          ((unsigned long long)(2u * a.epoch + 1u) << 32) | (before + tile_cnt));
+        // (after a wait that ran out, `before` is short: the outputs are then
+        // unspecified but every write stays in bounds, and the error word says so)
+      }
+      s_gbase[tid] = __ldg(a.digit_base + tid) + before - local_excl;
+    }
+
+    // ---- 5. write out the staged tile ----------------------------------------
+    __syncthreads();
+    const uint32_t n_valid = NINTH ? s_kept : uint32_t(TILE);  // a full tile keeps every row
+    bool bad = false;
+  #pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const uint32_t r = j * THREADS + tid;
+      if (!NINTH || r < n_valid) {
+        const uint32_t k = s_keys[r];
+        const V v = s_vals[r];
+        uint32_t d;
+        if (LEN_DIGIT) d = a.R.uniform_len - (uint32_t(v) & ((1u << a.R.shift) - 1u));
+        else d = (k >> a.key_shift) & (kRadix - 1);
+        const uint32_t g = s_gbase[d] + r;
+        const bool ok = g < a.n_out;
+        if (ok) vals_out[g] = v;
+        if (WRITE_KEY && ok) a.keys_out[g] = k;
+        bad = bad || !ok;
+      }
+    }
+    // Digit bases that disagree with the items: nothing was written out of bounds.
+    if (bad) atomicOr(a.err, kErrBounds);
+  };
+  if (FILTER || tile == a.n_tiles - 1) tile_body(std::true_type{});
+  else tile_body(std::false_type{});
 }
 
 // Tile shapes compiled in (threads, items per thread, CTAs per SM the register
