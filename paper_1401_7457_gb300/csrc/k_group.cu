@@ -32,39 +32,33 @@ namespace {
 
 constexpr int kChunk = 256;  // rows scanned per warp task
 
-// Word x of the store read as part of aligned 4-word chunks: chunk c holds
-// words 4c .. 4c+3 and is fetched with one 16-byte load when it lies wholly
-// inside the store (the store base is 16-byte aligned: checked by the host).
-__device__ __forceinline__ uint4 load_chunk(const ReadIndex& R, uint64_t c) {
-  if (4 * c + 3 < R.n_words) return __ldg(reinterpret_cast<const uint4*>(R.words) + c);
-  return make_uint4(load_word(R, 4 * c), load_word(R, 4 * c + 1), load_word(R, 4 * c + 2), load_word(R, 4 * c + 3));
-}
-
 // Bases [c0, c0 + 16*NW) of suffix s (A-padded past the read end) as NW words.
-// The NW + 1 store words it spans are fetched as at most NW/4 + 2 aligned
-// 16-byte chunks (one L1 request each) instead of word by word.
+// The NW + 1 store words it spans are fetched as NW/4 + 2 aligned 16-byte
+// chunks (one L1 request each) instead of word by word.  No branch depends on
+// the suffix: a window past the read's end fetches the read's first chunks and
+// is masked to zero, and the words past the end are masked the same way, so
+// the lanes of a warp stay together.
 template <int NW>
 __device__ __forceinline__ void gather_words(const ReadIndex& R, const Suffix& s, uint32_t c0, uint32_t (&w)[NW]) {
   const uint32_t rel = s.k + c0;
-  const uint32_t rem = rel < s.len ? s.len - rel : 0u;  // real bases from c0 on
-#pragma unroll
-  for (int i = 0; i < NW; ++i) w[i] = 0u;
-  if (rem == 0) return;
-  const uint64_t q = s.off + rel;
+  const bool inside = rel < s.len;
+  const uint32_t rem = inside ? s.len - rel : 0u;  // real bases from c0 on
+  const uint64_t q = s.off + (inside ? rel : 0u);
   const uint64_t w0 = q >> 4;
   const uint32_t sh = uint32_t(q & 15u) * 2u;
   const uint32_t o = uint32_t(w0 & 3u);  // offset of w0 in its chunk
   constexpr int CH = NW / 4 + 2;         // chunks covering words w0 .. w0 + NW
   uint32_t b[4 * CH];
-  const uint32_t words_needed = min(uint32_t(NW), (rem + 15u) / 16u) + 1u;
-  const uint32_t chunks = (o + words_needed + 3u) / 4u;
 #pragma unroll
   for (int c = 0; c < CH; ++c) {
-    uint4 x = make_uint4(0u, 0u, 0u, 0u);
-    if (uint32_t(c) < chunks) x = R.words_aligned ? load_chunk(R, (w0 >> 2) + c)
-                                                  : make_uint4(load_word(R, w0 - o + 4 * c), load_word(R, w0 - o + 4 * c + 1),
-                                                               load_word(R, w0 - o + 4 * c + 2),
-                                                               load_word(R, w0 - o + 4 * c + 3));
+    const uint64_t ci = (w0 >> 2) + c;
+    uint4 x;
+    if (R.words_aligned && 4 * ci + 3 < R.n_words) {
+      x = __ldg(reinterpret_cast<const uint4*>(R.words) + ci);
+    } else {  // an unaligned store, or its last (partial) chunk
+      x = make_uint4(load_word(R, 4 * ci), load_word(R, 4 * ci + 1), load_word(R, 4 * ci + 2),
+                     load_word(R, 4 * ci + 3));
+    }
     b[4 * c] = x.x; b[4 * c + 1] = x.y; b[4 * c + 2] = x.z; b[4 * c + 3] = x.w;
   }
   // Word i of the suffix window is store word w0 + i = b[o + i]: shift the
@@ -77,13 +71,12 @@ __device__ __forceinline__ void gather_words(const ReadIndex& R, const Suffix& s
   for (int i = 0; i < NW + 1; ++i) d[i] = (o & 1u) ? c[i + 1] : c[i];
 #pragma unroll
   for (int i = 0; i < NW; ++i) {
+    // Keep the first `left` bases of word i (none when left == 0: the shift
+    // by 0 keeps all ones).
     const uint32_t need = 16u * i;
-    if (need < rem) {
-      uint32_t x = __funnelshift_l(d[i + 1], d[i], sh);
-      const uint32_t left = rem - need;
-      if (left < 16u) x &= ~(0xFFFFFFFFu >> (2u * left));
-      w[i] = x;
-    }
+    const uint32_t left = rem > need ? rem - need : 0u;
+    const uint32_t keep = left >= 16u ? 0xFFFFFFFFu : ~(0xFFFFFFFFu >> (2u * left));
+    w[i] = __funnelshift_l(d[i + 1], d[i], sh) & keep;
   }
 }
 
