@@ -13,11 +13,13 @@
 //   1. take a tile id from an atomic counter (so every lower tile is already
 //      running: the look-back below always makes progress),
 //   2. load the tile (warp-striped, coalesced) and compute each item's digit,
-//   3. rank items inside the tile: warp-level ballots (one per digit bit)
-//      group equal digits; a per-warp shared-memory histogram accumulates
-//      counts in item order, so the ranking is stable,
-//   4. publish the tile's per-digit counts, stage the tile in shared memory
-//      in sorted order, and walk back over the predecessors' published counts
+//   3. count the tile's digits (shared-memory atomics) and publish the
+//      counts at once, so that successors rarely wait for them; then rank
+//      items inside the tile: warp-level ballots (one per digit bit) group
+//      equal digits; a per-warp shared-memory histogram accumulates counts in
+//      item order, so the ranking is stable,
+//   4. stage the tile in shared memory in sorted order, and walk back over
+//      the predecessors' published counts
 //      (decoupled look-back) to find, for each digit, how many items of
 //      earlier tiles precede this tile (the first look-back load is issued
 //      before the staging, so the two overlap); the first row of each digit
@@ -74,6 +76,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
   // Per-warp digit counts; after the look-back, the tile-local row of the
   // warp's first item of each digit.
   __shared__ uint32_t s_whist[WARPS][kRadix];
+  __shared__ uint32_t s_thist[kRadix];
   __shared__ uint32_t s_gbase[kRadix];  // global row of tile-local row 0 of each digit
   __shared__ uint32_t s_scan[8];
   __shared__ uint32_t s_tile, s_kept;
@@ -83,6 +86,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
   V* vals_out = static_cast<V*>(a.vals_out);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int i = tid; i < WARPS * kRadix; i += THREADS) (&s_whist[0][0])[i] = 0u;
+  for (int i = tid; i < kRadix; i += THREADS) s_thist[i] = 0u;
   if (MODE == kSrcCollection)
     for (uint32_t i = tid; i <= a.n_coll; i += THREADS) s_coll[i] = a.coll_start[i];
   if (tid == 0) {
@@ -189,6 +193,20 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
       // match only each other and are neither counted nor written.
       digit[j] = keep ? d : uint32_t(kRadix);
     }
+    // Tile counts first, published before the ranking: a successor's
+    // look-back then finds them already written.
+  #pragma unroll
+    for (int j = 0; j < IPT; ++j)
+      if (!NINTH || digit[j] < kRadix) atomicAdd(&s_thist[digit[j]], 1u);
+    __syncthreads();
+    uint32_t tile_cnt = 0;
+    if (tid < kRadix) {
+      tile_cnt = s_thist[tid];
+      const unsigned long long agg_flag = (unsigned long long)(2u * a.epoch) << 32;
+      const unsigned long long pre_flag = (unsigned long long)(2u * a.epoch + 1u) << 32;
+      if (!(tile == 0 && a.stall_tile0))
+        store_relaxed_u64(a.status + uint64_t(tile) * kRadix + tid, (tile == 0 ? pre_flag : agg_flag) | tile_cnt);
+    }
 
     // ---- 3. stable rank inside the warp, in item order ------------------------
     // Lanes holding the same digit are found with one ballot per digit bit (a
@@ -220,8 +238,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
     }
     __syncthreads();
 
-    // ---- 4. tile counts; stage sorted while the first look-back load is out --
-    uint32_t tile_cnt = 0;
+    // ---- 4. stage sorted while the first look-back load is out ---------------
     unsigned long long prev = 0;  // predecessor's status word, fetched before the staging
     if (tid < kRadix) {
       uint32_t sum = 0;
@@ -231,11 +248,6 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
         s_whist[w][tid] = sum;
         sum += c;
       }
-      tile_cnt = sum;
-      const unsigned long long agg_flag = (unsigned long long)(2u * a.epoch) << 32;
-      const unsigned long long pre_flag = (unsigned long long)(2u * a.epoch + 1u) << 32;
-      if (!(tile == 0 && a.stall_tile0))
-        store_relaxed_u64(a.status + uint64_t(tile) * kRadix + tid, (tile == 0 ? pre_flag : agg_flag) | tile_cnt);
     }
     const uint32_t local_excl = block_exclusive_scan_256<THREADS>(tile_cnt, s_scan);
     if (tid == kRadix - 1) s_kept = local_excl + tile_cnt;  // rows of this tile that are written
