@@ -94,6 +94,24 @@ __device__ __forceinline__ uint32_t window16(const ReadIndex& R, const Suffix& s
   return key;
 }
 
+// window16 for kernels that issue many gathers at once (a digit pass gathers
+// one window per item, 16 per thread): two 4-byte loads, no 16-byte chunk
+// (fewer registers held per load in flight) and no branch on the suffix (a
+// window past the read's end reads the read's first word and is masked to
+// zero), so the lanes of a warp stay together.
+__device__ __forceinline__ uint32_t window16_pair(const ReadIndex& R, const Suffix& s, uint32_t c0) {
+  const uint32_t rel = s.k + c0;
+  const bool inside = rel < s.len;
+  const uint32_t rem = inside ? s.len - rel : 0u;
+  const uint64_t q = s.off + (inside ? rel : 0u);
+  const uint64_t w = q >> 4;
+  const uint32_t sh = uint32_t(q & 15u) * 2u;
+  const uint32_t key = __funnelshift_l(load_word(R, w + 1), load_word(R, w), sh);
+  // Keep the first rem bases (none when rem == 0: the shift by 0 keeps all ones).
+  const uint32_t keep = rem >= 16u ? 0xFFFFFFFFu : ~(0xFFFFFFFFu >> (2u * rem));
+  return key & keep;
+}
+
 // Code (0..3) of the base at store position q.
 __device__ __forceinline__ uint32_t base_at(const ReadIndex& R, uint64_t q) {
   return (load_word(R, q >> 4) >> (30u - 2u * uint32_t(q & 15u))) & 3u;

@@ -32,12 +32,12 @@ namespace {
 
 constexpr int kChunk = 256;  // rows scanned per warp task
 
-// Bases [c0, c0 + 16*NW) of suffix s (A-padded past the read end) as NW words.
-// The NW + 1 store words it spans are fetched as NW/4 + 2 aligned 16-byte
-// chunks (one L1 request each) instead of word by word.  No branch depends on
-// the suffix: a window past the read's end fetches the read's first chunks and
-// is masked to zero, and the words past the end are masked the same way, so
-// the lanes of a warp stay together.
+// Bases [c0, c0 + 16*NW) of suffix s (A-padded past the read end) as NW words,
+// from the NW + 1 store words they span (4-byte loads: fewer registers held
+// per load in flight than 16-byte chunks, and no realignment of the chunks).
+// No branch depends on the suffix: a window past the read's end reads the
+// read's first words and is masked to zero, and the words past the end are
+// masked the same way, so the lanes of a warp stay together.
 template <int NW>
 __device__ __forceinline__ void gather_words(const ReadIndex& R, const Suffix& s, uint32_t c0, uint32_t (&w)[NW]) {
   const uint32_t rel = s.k + c0;
@@ -46,37 +46,15 @@ __device__ __forceinline__ void gather_words(const ReadIndex& R, const Suffix& s
   const uint64_t q = s.off + (inside ? rel : 0u);
   const uint64_t w0 = q >> 4;
   const uint32_t sh = uint32_t(q & 15u) * 2u;
-  const uint32_t o = uint32_t(w0 & 3u);  // offset of w0 in its chunk
-  constexpr int CH = NW / 4 + 2;         // chunks covering words w0 .. w0 + NW
-  uint32_t b[4 * CH];
+  uint32_t b[NW + 1];
 #pragma unroll
-  for (int c = 0; c < CH; ++c) {
-    const uint64_t ci = (w0 >> 2) + c;
-    uint4 x;
-    if (R.words_aligned && 4 * ci + 3 < R.n_words) {
-      x = __ldg(reinterpret_cast<const uint4*>(R.words) + ci);
-    } else {  // an unaligned store, or its last (partial) chunk
-      x = make_uint4(load_word(R, 4 * ci), load_word(R, 4 * ci + 1), load_word(R, 4 * ci + 2),
-                     load_word(R, 4 * ci + 3));
-    }
-    b[4 * c] = x.x; b[4 * c + 1] = x.y; b[4 * c + 2] = x.z; b[4 * c + 3] = x.w;
-  }
-  // Word i of the suffix window is store word w0 + i = b[o + i]: shift the
-  // fetched words down by o in two steps (by 2, then by 1: a logarithmic
-  // shifter, one select per word and step) instead of indexing registers.
-  uint32_t c[NW + 2], d[NW + 1];
-#pragma unroll
-  for (int i = 0; i < NW + 2; ++i) c[i] = (o & 2u) ? b[i + 2] : b[i];
-#pragma unroll
-  for (int i = 0; i < NW + 1; ++i) d[i] = (o & 1u) ? c[i + 1] : c[i];
+  for (int i = 0; i <= NW; ++i) b[i] = load_word(R, w0 + i);
 #pragma unroll
   for (int i = 0; i < NW; ++i) {
-    // Keep the first `left` bases of word i (none when left == 0: the shift
-    // by 0 keeps all ones).
     const uint32_t need = 16u * i;
     const uint32_t left = rem > need ? rem - need : 0u;
     const uint32_t keep = left >= 16u ? 0xFFFFFFFFu : ~(0xFFFFFFFFu >> (2u * left));
-    w[i] = __funnelshift_l(d[i + 1], d[i], sh) & keep;
+    w[i] = __funnelshift_l(b[i + 1], b[i], sh) & keep;
   }
 }
 

@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
   #pragma unroll
       for (int j = 0; j < IPT; ++j) {
         const I idx = warp_base + j * 32;
-        key[j] = (!NINTH || idx < n_in) ? window16(a.R, decode(a.R, val[j]), a.window_c0) : 0u;
+        key[j] = (!NINTH || idx < n_in) ? window16_pair(a.R, decode(a.R, val[j]), a.window_c0) : 0u;
       }
     }
   #pragma unroll
