@@ -96,6 +96,11 @@ typedef struct {
  *                store would fit L2. */
 #define CXBWT_PLAN_ID64 1
 #define CXBWT_PLAN_READ_MAJOR 2
+/*  CARRY_BASE  - for reads of one length, carry the base before each suffix
+ *                in its id from the first digit pass on, so that writing B_R
+ *                gathers nothing from the store; by default only when the
+ *                store is larger than 64 MB (out of L2). */
+#define CXBWT_PLAN_CARRY_BASE 8
 /* Test hook for failure handling: in the first digit pass of a build, tile 0
  * does not publish its counts, so tile 1's look-back wait runs out (after
  * wait_limit_ms).  The build then returns CXBWT_ETIMEOUT with unspecified

@@ -264,8 +264,17 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   pl.n = n;
   std::vector<uint32_t> lens_copy;
   const uint32_t* hlens = lens_dev ? nullptr : lens;
+  // Lengths in pinned host memory are scanned on the device (one fast copy
+  // and a reduction instead of a serial host loop); pageable ones on the host.
+  const uint32_t* dlens = lens_dev ? lens : nullptr;
+  if (hlens && is_pinned_ptr(hlens)) {
+    CX_TRY(ensure(c, c->desc, n * 4, "read lengths"));
+    CX_CUDA(c, cudaMemcpyAsync(c->desc.p, hlens, n * 4, cudaMemcpyHostToDevice, st));
+    h2d += n * 4;
+    dlens = static_cast<const uint32_t*>(c->desc.p);
+  }
   uint64_t mn = ~0ull, mx = 0, sum = 0, bad = 0;
-  if (hlens) {
+  if (!dlens) {
     for (uint64_t i = 0; i < n; ++i) {
       const uint32_t L = hlens[i];
       mn = std::min<uint64_t>(mn, L);
@@ -276,7 +285,7 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   } else {
     const unsigned long long init[4] = {~0ull, 0, 0, 0};
     CX_CUDA(c, cudaMemcpyAsync(d_lstats, init, sizeof init, cudaMemcpyHostToDevice, st));
-    CX_CUDA(c, launch_lenstats(lens, n, d_lstats, st));
+    CX_CUDA(c, launch_lenstats(dlens, n, d_lstats, st));
     ++r.launches;
     CX_CUDA(c, cudaMemcpyAsync(c->h_small, d_lstats, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CX_CUDA(c, cudaStreamSynchronize(st));
@@ -318,9 +327,8 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   // Windows [0, w_last] are sorted by LSD passes over all rows; with the
   // group plan only window 0 is, and the groups are finished on chip.
   pl.w_last = pl.groups ? 0u : pl.W - 1;
-  const uint64_t max_id = ((n - 1) << pl.shift) | pl.Lmax;
-  pl.idb = (pl.shift <= 31 && ((n - 1) >> (32 - pl.shift)) == 0 && max_id <= 0xFFFFFFFFull) ? 4 : 8;
-  if (c->opt.plan_flags & CXBWT_PLAN_ID64) pl.idb = 8;
+  plan_ids(pl, (c->opt.plan_flags & CXBWT_PLAN_ID64) != 0,
+           pl.n_words * 4 > (64u << 20) || (c->opt.plan_flags & CXBWT_PLAN_CARRY_BASE));
   r.shape = onesweep_shape(tile_items, pl.idb);
   const uint32_t TILE = uint32_t(r.shape.tile());
 
@@ -376,7 +384,7 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
     d_desc = static_cast<const uint64_t*>(c->desc.p);
   }
   r.R = ReadIndex{d_reads, pl.n_words, d_desc, pl.shift, pl.uniform ? pl.Lmax : 0u, uint32_t(n),
-                  (reinterpret_cast<uintptr_t>(d_reads) & 15u) == 0 ? 1u : 0u};
+                  (reinterpret_cast<uintptr_t>(d_reads) & 15u) == 0 ? 1u : 0u, pl.sym};
 
   // ---- slices --------------------------------------------------------------
   // Device bytes per suffix of a slice: ids and keys (double-buffered),

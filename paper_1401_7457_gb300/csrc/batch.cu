@@ -84,9 +84,7 @@ int build_pack(cxbwt_ctx* c, const cxbwt_collection* colls, const std::vector<ui
   pl.seg_words = segsort_words(L);
   pl.groups = true;
   pl.w_last = 0;
-  const uint64_t max_id = ((pl.n - 1) << pl.shift) | L;
-  pl.idb = (((pl.n - 1) >> (32 - pl.shift)) == 0 && max_id <= 0xFFFFFFFFull) ? 4 : 8;
-  if (c->opt.plan_flags & CXBWT_PLAN_ID64) pl.idb = 8;
+  plan_ids(pl, (c->opt.plan_flags & CXBWT_PLAN_ID64) != 0, (c->opt.plan_flags & CXBWT_PLAN_CARRY_BASE) != 0);
   r.shape = onesweep_shape(c->opt.tile_items, pl.idb);
   const uint32_t TILE = uint32_t(r.shape.tile());
 
@@ -112,7 +110,7 @@ int build_pack(cxbwt_ctx* c, const cxbwt_collection* colls, const std::vector<ui
   const uint32_t desc_blocks = uint32_t(std::min<uint64_t>((pl.n + 255) / 256, uint64_t(c->sm_count) * 8));
   k_pack_desc<<<desc_blocks, 256, 0, st>>>(static_cast<uint64_t*>(c->desc.p), uint32_t(pl.n), d_cs, d_cw, k, L);
   CX_CUDA(c, cudaGetLastError());
-  r.R = ReadIndex{store, words, static_cast<const uint64_t*>(c->desc.p), pl.shift, L, uint32_t(pl.n), 1u};
+  r.R = ReadIndex{store, words, static_cast<const uint64_t*>(c->desc.p), pl.shift, L, uint32_t(pl.n), 1u, pl.sym};
 
   // ---- workspace ---------------------------------------------------------
   char* misc = static_cast<char*>(c->misc.p);

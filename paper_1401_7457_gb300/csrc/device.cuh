@@ -1,9 +1,13 @@
 // Device-side building blocks shared by the cxbwt kernels.
 //
 // Suffix encoding.  A suffix S_i[k..] $_i is carried through the sort as one
-// id v = (i << shift) | k, with 2^shift > max L_i so that k in [0, L_i]
-// fits; the id is 32 bits while n * 2^shift < 2^32, else 64 bits.  Moving these values instead of the suffixes is the paper's
-// "sort by index" (Section 3.2).
+// id v = (i << shift) | (k << sym_bits) | sym, with 2^(shift - sym_bits) >
+// max L_i so that k in [0, L_i] fits; the id is 32 bits while n * 2^shift <
+// 2^32, else 64 bits.  Moving these values instead of the suffixes is the
+// paper's "sort by index" (Section 3.2).  When sym_bits is 2 (reads of one
+// length: the first digit pass generates the ids), sym is the code of the
+// base before the suffix, S_i[k-1] (0 when k = 0), gathered while the ids are
+// made, so that writing the BWT needs no second gather.
 //
 // Read store.  Bases are 2-bit codes, most significant first, reads
 // concatenated (the ABI layout).  The offset and length of read i are either
@@ -36,6 +40,7 @@ struct ReadIndex {
   uint32_t uniform_len;   // L when desc == nullptr
   uint32_t n_reads;
   uint32_t words_aligned; // nonzero when `words` is 16-byte aligned (vector loads allowed)
+  uint32_t sym_bits;      // 2 when ids carry the preceding base in their low bits, else 0
 };
 
 struct Suffix {
@@ -49,7 +54,7 @@ template <class V>
 __device__ __forceinline__ Suffix decode(const ReadIndex& R, V v) {
   Suffix s;
   s.read = uint32_t(v >> R.shift);
-  s.k = uint32_t(v) & ((1u << R.shift) - 1u);
+  s.k = (uint32_t(v) & ((1u << R.shift) - 1u)) >> R.sym_bits;
   if (R.desc) {
     // The clamp only matters for a corrupted value; it keeps the load in bounds.
     const uint64_t d = __ldg(R.desc + min(s.read, R.n_reads - 1u));
@@ -109,6 +114,26 @@ __device__ __forceinline__ uint32_t window16_pair(const ReadIndex& R, const Suff
   const uint32_t key = __funnelshift_l(load_word(R, w + 1), load_word(R, w), sh);
   // Keep the first rem bases (none when rem == 0: the shift by 0 keeps all ones).
   const uint32_t keep = rem >= 16u ? 0xFFFFFFFFu : ~(0xFFFFFFFFu >> (2u * rem));
+  return key & keep;
+}
+
+// window16_pair of the suffix's first window (c0 = 0) that also returns the
+// base before the suffix (S_i[k-1], 0 when k = 0).  It lies in the first word
+// the window already loaded unless the suffix starts a store word (or is the
+// terminator-only one): only then is one more word loaded.
+__device__ __forceinline__ uint32_t window16_pair_prev(const ReadIndex& R, const Suffix& s, uint32_t* prev) {
+  const bool inside = s.k < s.len;
+  const uint32_t rem = inside ? s.len - s.k : 0u;
+  const uint64_t q = s.off + (inside ? s.k : 0u);
+  const uint64_t w = q >> 4;
+  const uint32_t sh = uint32_t(q & 15u) * 2u;
+  const uint32_t w0 = load_word(R, w);
+  const uint32_t key = __funnelshift_l(load_word(R, w + 1), w0, sh);
+  const uint32_t keep = rem >= 16u ? 0xFFFFFFFFu : ~(0xFFFFFFFFu >> (2u * rem));
+  const uint64_t qp = s.off + s.k - 1;  // meaningful for k > 0
+  const uint64_t wp = qp >> 4;
+  const uint32_t wordp = (s.k == 0u || wp == w) ? w0 : load_word(R, wp);
+  *prev = s.k ? (wordp >> (30u - 2u * uint32_t(qp & 15u))) & 3u : 0u;
   return key & keep;
 }
 

@@ -126,6 +126,16 @@ inline bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+inline bool is_pinned_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
 // misc buffer layout (bytes)
 constexpr size_t kMiscTileCounter = 0;   // uint32
 constexpr size_t kMiscErr = 4;           // uint32
@@ -151,10 +161,35 @@ struct Plan {
   uint32_t len_passes = 0;
   uint64_t n_words = 0;
   int idb = 4;            // suffix id bytes
+  uint32_t sym = 0;       // id bits holding the preceding base (0 or 2)
   bool groups = false;
   int seg_words = 0;
   uint32_t w_last = 0;    // windows [0, w_last] are sorted by LSD passes over all rows of a slice
 };
+
+// Id layout of a build: (read << shift) | (k << sym) | preceding base.  The
+// preceding base rides along (sym = 2) when the emission would otherwise
+// gather it from a store in HBM (want_sym: a store larger than L2) and the
+// reads have one length (the first digit pass generates their ids), unless
+// those two bits would push 32-bit ids to 64 bits; ids are 64-bit only when
+// 32 bits cannot hold (read, k).  (With the store in L2 the gather is cheaper
+// than carrying the base through the first pass.)
+inline void plan_ids(Plan& pl, bool force64, bool want_sym) {
+  const uint32_t len_bits = bits_for(pl.Lmax);
+  const bool sym_ok = want_sym && pl.uniform;
+  auto fits32 = [&](uint32_t sh) { return sh <= 31 && ((pl.n - 1) >> (32 - sh)) == 0; };
+  if (!force64 && sym_ok && fits32(len_bits + 2)) {
+    pl.idb = 4;
+    pl.sym = 2;
+  } else if (!force64 && fits32(len_bits)) {
+    pl.idb = 4;
+    pl.sym = 0;
+  } else {
+    pl.idb = 8;
+    pl.sym = sym_ok ? 2 : 0;
+  }
+  pl.shift = len_bits + pl.sym;
+}
 
 struct Slice {
   bool whole = true;          // every suffix (no bucket filter)

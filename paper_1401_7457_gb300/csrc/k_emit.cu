@@ -3,8 +3,9 @@
 // that a suffix starting at position 0 is preceded by $.
 //
 // Each thread owns one packed output word (16 consecutive global rows), so it
-// assembles the word by itself: up to 16 sorted ids, 16 gathers of the
-// preceding base from the (L2-resident) read store, one 4-byte store.  A
+// assembles the word by itself: up to 16 sorted ids, the preceding base of
+// each (carried in the id when the ids were generated with it, else gathered
+// from the read store), one 4-byte store.  A
 // slice of the BWT (one HBM-bounded pass) may start or end inside a word:
 // those two words are merged with atomicOr into a word the host zeroed.
 // Alongside it records where each read's $ landed and counts the symbols.
@@ -65,7 +66,8 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const EmitArgs a) {
           cpack += 1ull;
           if (a.dollar_pos) a.dollar_pos[s.read - a.read_base] = g;
         } else {
-          sym = base_at(a.R, s.off + s.k - 1);
+          // The id carries the preceding base when the ids were generated with it.
+          sym = a.R.sym_bits ? uint32_t(v[j]) & 3u : base_at(a.R, s.off + s.k - 1);
           cpack += 1ull << (8 * (sym + 1));
         }
         word |= sym << (30 - 2 * j);

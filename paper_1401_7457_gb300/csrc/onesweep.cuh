@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
       uint32_t i = uint32_t(warp_base - slen0 * n);
   #pragma unroll
       for (int j = 0; j < IPT; ++j) {
-        val[j] = (V(i) << a.R.shift) | V(L - min(slen, L));
+        val[j] = (V(i) << a.R.shift) | (V(L - min(slen, L)) << a.R.sym_bits);
         i += 32;
         while (i >= n) {  // once per step when n >= 32
           i -= n;
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
       V i = V(i0);
   #pragma unroll
       for (int j = 0; j < IPT; ++j) {
-        val[j] = (i << a.R.shift) | V(k);
+        val[j] = (i << a.R.shift) | (V(k) << a.R.sym_bits);
         k += 32;
         while (k >= L1) {
           k -= L1;
@@ -174,6 +174,25 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
         }
         key[j] = lo;
       }
+    } else if (GEN && a.R.sym_bits) {
+      // Generated ids take the base before the suffix into their low bits
+      // (one branch per tile: the plain gather below keeps its own loop).
+  #pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        const I idx = warp_base + j * 32;
+        key[j] = 0u;
+        if (!NINTH || idx < n_in) {
+          const Suffix sfx = decode(a.R, val[j]);
+          uint32_t prev;
+          if (a.window_c0 == 0) {
+            key[j] = window16_pair_prev(a.R, sfx, &prev);
+          } else {
+            key[j] = window16_pair(a.R, sfx, a.window_c0);
+            prev = sfx.k ? base_at(a.R, sfx.off + sfx.k - 1) : 0u;
+          }
+          val[j] |= V(prev);
+        }
+      }
     } else {
   #pragma unroll
       for (int j = 0; j < IPT; ++j) {
@@ -187,7 +206,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
       bool keep = !NINTH || idx < n_in;
       if (FILTER) keep = keep && ((key[j] >> a.bucket_shift) - a.bucket_lo) < (a.bucket_hi - a.bucket_lo);
       uint32_t d;
-      if (LEN_DIGIT) d = a.R.uniform_len - (uint32_t(val[j]) & ((1u << a.R.shift) - 1u));
+      if (LEN_DIGIT) d = a.R.uniform_len - ((uint32_t(val[j]) & ((1u << a.R.shift) - 1u)) >> a.R.sym_bits);
       else d = (key[j] >> a.key_shift) & (kRadix - 1);
       // Rows past the end (or filtered out) get a value no digit has, so they
       // match only each other and are neither counted nor written.
@@ -317,7 +336,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
         const uint32_t k = s_keys[r];
         const V v = s_vals[r];
         uint32_t d;
-        if (LEN_DIGIT) d = a.R.uniform_len - (uint32_t(v) & ((1u << a.R.shift) - 1u));
+        if (LEN_DIGIT) d = a.R.uniform_len - ((uint32_t(v) & ((1u << a.R.shift) - 1u)) >> a.R.sym_bits);
         else d = (k >> a.key_shift) & (kRadix - 1);
         const uint32_t g = s_gbase[d] + r;
         const bool ok = g < a.n_out;

@@ -237,3 +237,44 @@ def test_long_reads_group_plan(length, n):
     codes, lens = synth.sample_reads(g, n, length, length + 1, 0.01)
     with binding.Context(device=0, algorithm=2) as c:
         assert_same(gpu_bwt(c, codes, lens, want_sa=True), oracle_of(codes, lens), sa=True)
+
+
+@pytest.mark.parametrize("flags,algorithm", [(8, 1), (8, 2), (8 | 1, 1), (8 | 1, 2), (8 | 2, 2), (8 | 2 | 1, 2)])
+def test_carried_base_plans(flags, algorithm):
+    """Ids that carry the base before the suffix (the default for stores out of
+    L2), forced on small inputs: 32- and 64-bit ids, read-major slices, both
+    sort plans (the LSD plan's first pass gathers the last window, not the
+    first); slices (a small budget) run with the group plan only."""
+    from paper_1401_7457_gb300 import binding
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    g = synth.random_genome(40_000, 71)
+    codes, lens = synth.sample_reads(g, 6000, 100, 72, 0.01)
+    ref = oracle_of(codes, lens)
+    N = int(lens.sum()) + lens.size
+    budget = (6 << 20) + int((28 if flags & 1 else 20) * N / 3) if flags & 2 else 0
+    with binding.Context(device=0, algorithm=algorithm, plan_flags=flags, budget_bytes=budget) as c:
+        got = gpu_bwt(c, codes, lens, want_sa=True)
+    assert_same(got, ref, sa=True)
+
+
+def test_carried_base_batch():
+    from paper_1401_7457_gb300 import binding
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    cols = []
+    for j in range(5):
+        codes, lens = synth.uniform_reads(300 + 100 * j, 36 if j % 2 else 76, 80 + j)
+        cols.append((codes, lens))
+    with binding.Context(device=0, plan_flags=8) as c:
+        outs = []
+        for codes, lens in cols:
+            n_sym = int(lens.sum()) + lens.size
+            outs.append((binding.pack_codes(codes), np.ascontiguousarray(lens, dtype=np.uint32),
+                         np.zeros((n_sym + 15) // 16, dtype=np.uint32), np.zeros(lens.size, dtype=np.uint64),
+                         np.zeros(5, dtype=np.uint64)))
+        c.build_batch(outs)
+    for (codes, lens), (_, _, bwt, dpos, cnt) in zip(cols, outs):
+        ref = oracle_of(codes, lens)
+        assert binding.unpack_ascii(bwt, dpos, len(ref["bwt"])) == ref["bwt"]
+        assert np.array_equal(dpos, ref["dollar_pos"]) and np.array_equal(cnt, ref["counts"])
