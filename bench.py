@@ -61,7 +61,6 @@ def load_workload(name, rank=0, n_reads=0):
         seed = 1 if rank == 0 else synth.derive_seed(1, rank)
         codes, lens = synth.uniform_reads(n_reads or 10_000, 100, seed)
     return WORKLOADS[name], codes, lens
-SORT_BYTES_PER_ITEM = 16  # algorithmic bytes per suffix per digit pass: 4 B key + 4 B id, read and written
 PROFILE = os.path.join(ROOT, "profiles", "onesweep_digit_pass_genome_like.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_1401_7457_gb300", "csrc", "onesweep.cuh")
 FALLBACK_HBM_GBS = 6800.0
@@ -81,6 +80,17 @@ def peak_hbm():
             return float(json.load(f)["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+def id_bytes(n_reads: int, read_len: int, store_bytes: int) -> int:
+    """Suffix id width the library picks for reads of one length: (read, k)
+    in 32 bits when they fit, plus two bits for the preceding base when the
+    store is larger than 64 MB (and those still fit)."""
+    len_bits = max(read_len, 1).bit_length()
+    sym = 2 if store_bytes > (64 << 20) else 0
+    if sym and (n_reads - 1) < (1 << (32 - len_bits - sym)):
+        return 4
+    return 4 if (n_reads - 1) < (1 << (32 - len_bits)) else 8
 
 
 def profiled_traffic():
@@ -575,19 +585,23 @@ def main():
     st = ctx.stats()
     value, total_ms = aggregate(dist, sum(ms), bases, world, args.steps)
 
-    # Dominant kernel: the onesweep digit pass.
+    # Dominant kernel: the onesweep digit pass.  Its algorithmic bytes per
+    # item are the key (4 B) and the id (4 or 8 B), read and written.
+    idb = id_bytes(n, int(lens.max()), int((int(lens.sum()) + 15) // 16) * 4)
+    bytes_per_item = 2 * (4 + idb)
     launches = max(st["sort_pass_launches"], 1)
     pass_ms = st["sort_pass_ms"] / launches
     items_per_launch = st["sort_pass_items"] / launches  # N per launch for a one-slice build
-    achieved = SORT_BYTES_PER_ITEM * items_per_launch / (pass_ms * 1e-3) / 1e9 if pass_ms > 0 else 0.0
+    achieved = bytes_per_item * items_per_launch / (pass_ms * 1e-3) / 1e9 if pass_ms > 0 else 0.0
     peak, peak_kind = peak_hbm()
-    traffic_per_item = profiled_traffic()
+    # The committed ncu summary covers 32-bit ids.
+    traffic_per_item = profiled_traffic() if idb == 4 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None if traffic_per_item is None else traffic_per_item * items_per_launch,
                 "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s",
                 "kernel": "k_onesweep (LSD digit pass)", "launches_per_step": st["sort_pass_launches"] / args.steps,
-                "algorithmic_bytes_per_launch": SORT_BYTES_PER_ITEM * items_per_launch,
+                "algorithmic_bytes_per_launch": bytes_per_item * items_per_launch,
                 "avg_launch_ms": pass_ms, "frac_of_nominal_8tbs": achieved / 8000.0}
     launches_per_step = st["kernel_launches"] / args.steps
 
@@ -642,7 +656,10 @@ def main():
                            "sort_pass_ms_per_step": st["sort_pass_ms"] / args.steps,
                            "group_finish_ms_per_step": st["group_ms"] / args.steps,
                            "emit_ms_per_step": st["emit_ms"] / args.steps,
-                           "build_ms_per_step_lib": st["build_ms"] / args.steps}}
+                           "build_ms_per_step_lib": st["build_ms"] / args.steps,
+                           "id_bytes": idb,
+                           "cta_groups_per_step": st["cta_groups"] / args.steps,
+                           "big_groups_per_step": st["big_groups"] / args.steps}}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

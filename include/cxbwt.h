@@ -134,7 +134,9 @@ typedef struct {
   double group_ms;              /* device time finishing groups (group plan, only with `timing`) */
   double emit_ms;               /* device time of the emission (only with `timing`) */
   uint64_t slices;              /* device-memory-bounded slices sorted (one per build when it fits) */
-  uint64_t reserved[4];
+  uint64_t cta_groups;          /* groups of equal first 16 bases finished by one CTA (33 .. 2048 rows) */
+  uint64_t big_groups;          /* larger groups, finished with more digit passes */
+  uint64_t reserved[2];
 } cxbwt_stats;
 
 /* ABI version of the loaded library (CXBWT_ABI_VERSION it was built with). */

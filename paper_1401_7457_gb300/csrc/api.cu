@@ -155,7 +155,7 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
   // ---- group plan: finish every group of equal first windows on chip ---------
   if (pl.groups && pl.Lmax > 16) {
     const uint64_t cta_cap = uint64_t(sl.rows) / 33 + 1, big_cap = uint64_t(sl.rows) / kCtaMax + 1;
-    CX_CUDA(c, cudaMemsetAsync(r.d_seg, 0, 16, st));
+    CX_CUDA(c, cudaMemsetAsync(r.d_seg, 0, 32, st));
     SegArgs g{};
     g.keys = r.keys[kin];
     g.vals = r.vals[cur];
@@ -172,9 +172,12 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
     r.launches += 2;
     // Remainders too large for one CTA (rare: long runs of equal bases) are
     // finished here with LSD passes over bases 16.. restricted to their rows.
-    CX_CUDA(c, cudaMemcpyAsync(c->h_small + 5, r.d_seg, 8, cudaMemcpyDeviceToHost, st));
+    CX_CUDA(c, cudaMemcpyAsync(c->h_small + 5, r.d_seg, 16, cudaMemcpyDeviceToHost, st));
     CX_CUDA(c, cudaStreamSynchronize(st));
     const uint32_t n_big = std::min<uint32_t>(reinterpret_cast<const uint32_t*>(c->h_small + 5)[1], g.big_cap);
+    c->stats.cta_groups += uint64_t(reinterpret_cast<const uint32_t*>(c->h_small + 5)[0]) +
+                           reinterpret_cast<const uint32_t*>(c->h_small + 5)[3];
+    c->stats.big_groups += n_big;
     if (n_big) {
       std::vector<uint2> big(n_big);
       CX_CUDA(c, cudaMemcpyAsync(big.data(), g.big_list, n_big * 8, cudaMemcpyDeviceToHost, st));

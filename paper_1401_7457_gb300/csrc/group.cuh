@@ -7,6 +7,7 @@
 namespace cxbwt {
 
 constexpr uint32_t kCtaMax = 2048;  // largest group remainder finished by one CTA (keys of at most 16 words)
+constexpr uint32_t kSmallCta = 256; // remainders up to this size go to small CTAs (128 threads, many per SM)
 // The CTA finish holds (id, key words, index) per row in shared memory: wide
 // keys (long reads) get fewer rows.
 template <int NW>
@@ -24,7 +25,8 @@ struct SegArgs {
   uint32_t cta_cap;
   uint2* big_list;        // remainders of more rows, finished by the host
   uint32_t big_cap;
-  uint32_t* counts;       // [0] cta_list length, [1] big_list length, [2] CTA work counter (zero on entry)
+  uint32_t* counts;       // zero on entry: [0] small remainders (cta_list front), [1] big_list length,
+                          // [2] small work counter, [3] larger CTA remainders (cta_list back), [4] their work counter
   uint32_t* err;
 };
 

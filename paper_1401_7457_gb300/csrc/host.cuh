@@ -141,7 +141,7 @@ constexpr size_t kMiscTileCounter = 0;   // uint32
 constexpr size_t kMiscErr = 4;           // uint32
 constexpr size_t kMiscCounts = 64;       // 5 x uint64
 constexpr size_t kMiscLenStats = 128;    // 4 x uint64
-constexpr size_t kMiscSeg = 192;         // 4 x uint32: group-finish list lengths and work counter
+constexpr size_t kMiscSeg = 192;         // 8 x uint32: group-finish list lengths and work counters
 constexpr size_t kMiscBytes = 256;
 
 inline uint32_t bits_for(uint32_t x) {  // smallest s with 2^s > x

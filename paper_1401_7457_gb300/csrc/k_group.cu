@@ -228,10 +228,19 @@ __device__ void finish_long_group(const SegArgs& a, uint32_t gs, uint32_t ge, in
   if (m <= 32) {
     warp_rank_window<NW, V>(a, lo, m, 0u, m, true, lane, sw);
   } else if (lane == 0) {
-    const bool cta = m <= CtaRows<NW>::value;
-    const uint32_t slot = atomicAdd(a.counts + (cta ? 0 : 1), 1u);
-    if (slot < (cta ? a.cta_cap : a.big_cap)) (cta ? a.cta_list : a.big_list)[slot] = make_uint2(lo, m);
-    else atomicOr(a.err, kErrBounds);
+    // Up to kSmallCta rows: cta_list from the front (counts[0]); up to
+    // CtaRows: cta_list from the back (counts[3]; the two never meet, as each
+    // listed group holds more than 32 of the n_items rows); larger: big_list.
+    if (m <= CtaRows<NW>::value) {
+      const bool small = m <= kSmallCta;
+      const uint32_t slot = atomicAdd(a.counts + (small ? 0 : 3), 1u);
+      if (slot < a.cta_cap) a.cta_list[small ? slot : a.cta_cap - 1 - slot] = make_uint2(lo, m);
+      else atomicOr(a.err, kErrBounds);
+    } else {
+      const uint32_t slot = atomicAdd(a.counts + 1, 1u);
+      if (slot < a.big_cap) a.big_list[slot] = make_uint2(lo, m);
+      else atomicOr(a.err, kErrBounds);
+    }
   }
 }
 
@@ -281,24 +290,29 @@ __global__ void __launch_bounds__(256) k_segsort_warp(const SegArgs a) {
   }
 }
 
-// Shared-memory bitonic sort of one listed group per CTA (33 .. kCtaMax members).
-template <int NW, class V>
-__global__ void __launch_bounds__(512) k_segsort_cta(const SegArgs a) {
-  constexpr uint32_t kRows = CtaRows<NW>::value;
+// Shared-memory bitonic sort of one listed group per CTA, for groups of up to
+// ROWS members.  The groups come from a list of n_ptr[0] entries, read from
+// the front (dir > 0) or from the back of a list of cap entries (dir < 0);
+// *work hands them out.  Groups of up to kSmallCta rows run in small CTAs,
+// many per SM, so that the latency of their loads and barriers overlaps.
+template <int NW, class V, uint32_t ROWS, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_segsort_cta(const SegArgs a, const uint2* list, const uint32_t* n_ptr,
+                                                         uint32_t cap, int dir, uint32_t* work) {
+  constexpr uint32_t kRows = ROWS;
   extern __shared__ __align__(16) uint32_t sm[];
   V* vals = static_cast<V*>(a.vals);
   V* s_v = reinterpret_cast<V*>(sm);                                // [kRows]
   uint32_t* s_w = reinterpret_cast<uint32_t*>(s_v + kRows);         // [NW][kRows]
   uint16_t* s_perm = reinterpret_cast<uint16_t*>(s_w + NW * kRows);  // [kRows]
   __shared__ uint32_t s_item;
-  const uint32_t n_list = min(*(volatile uint32_t*)(a.counts + 0), a.cta_cap);
+  const uint32_t n_list = min(*(volatile const uint32_t*)n_ptr, cap);
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) s_item = atomicAdd(a.counts + 2, 1u);
+    if (threadIdx.x == 0) s_item = atomicAdd(work, 1u);
     __syncthreads();
     const uint32_t it = s_item;
     if (it >= n_list) break;
-    const uint2 g = a.cta_list[it];
+    const uint2 g = dir > 0 ? list[it] : list[cap - 1 - it];
     const uint32_t s = g.x, m = g.y;
     uint32_t P = 64;
     while (P < m) P <<= 1;
@@ -389,6 +403,23 @@ __global__ void __launch_bounds__(kRadix) k_scan256(uint32_t* hist) {
   hist[row * kRadix + v] = s[v];
 }
 
+template <int NW, class V, uint32_t ROWS, int THREADS>
+cudaError_t launch_cta_nw(const SegArgs& a, uint32_t grid, const uint2* list, const uint32_t* n_ptr, uint32_t cap,
+                          int dir, uint32_t* work, cudaStream_t st) {
+  const size_t smem = size_t(ROWS) * (sizeof(V) + NW * 4 + 2);
+  auto kern = k_segsort_cta<NW, V, ROWS, THREADS>;
+  static bool configured = false;  // per instantiation
+  if (!configured) {
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  kern<<<grid, THREADS, smem, st>>>(a, list, n_ptr, cap, dir, work);
+  return cudaGetLastError();
+}
+
+// The warp kernel, then the small-group and the large-group CTA kernels over
+// the two ends of the list it fills.
 template <int NW, class V>
 cudaError_t launch_nw(const SegArgs& a, int sm_count, cudaStream_t st) {
   const uint32_t n_chunks = (a.n_items + kChunk - 1) / kChunk;
@@ -399,15 +430,11 @@ cudaError_t launch_nw(const SegArgs& a, int sm_count, cudaStream_t st) {
   k_segsort_warp<NW, V><<<blocks, 256, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t smem = size_t(CtaRows<NW>::value) * (sizeof(V) + NW * 4 + 2);
-  static bool configured = false;
-  if (!configured) {
-    e = cudaFuncSetAttribute(k_segsort_cta<NW, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  k_segsort_cta<NW, V><<<sm_count * 2, 512, smem, st>>>(a);
-  return cudaGetLastError();
+  e = launch_cta_nw<NW, V, kSmallCta, 128>(a, uint32_t(sm_count) * 16, a.cta_list, a.counts + 0, a.cta_cap, 1,
+                                           a.counts + 2, st);
+  if (e != cudaSuccess) return e;
+  return launch_cta_nw<NW, V, CtaRows<NW>::value, 512>(a, uint32_t(sm_count) * 2, a.cta_list, a.counts + 3,
+                                                        a.cta_cap, -1, a.counts + 4, st);
 }
 
 template <class V>
