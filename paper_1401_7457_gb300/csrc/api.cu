@@ -49,7 +49,7 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
   a.R = r.R;
   a.n_reads = uint32_t(pl.n);
   a.timeout_ns = c->opt.wait_limit_ms > 0 ? uint64_t(c->opt.wait_limit_ms) * 1000000ull : kTimeoutNs;
-  a.bucket_shift = 32 - kBucketBits;
+  a.bucket_shift = 32 - r.bucket_bits;
   a.bucket_lo = sl.lo;
   a.bucket_hi = sl.hi;
   const uint32_t d_sorted = std::min<uint32_t>(pl.D, 4 * (pl.w_last + 1));
@@ -65,7 +65,7 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
     r.launches += 2;
   } else {
     CX_CUDA(c, cudaMemsetAsync(r.base, 0, 5 * kRadix * 4, st));
-    CX_CUDA(c, launch_pass_hist(r.R, uint32_t(pl.n), kBucketBits, sl.lo, sl.hi, r.base, c->sm_count, st));
+    CX_CUDA(c, launch_pass_hist(r.R, uint32_t(pl.n), r.bucket_bits, sl.lo, sl.hi, r.base, c->sm_count, st));
     r.launches += 2;
   }
   auto digit_base = [&](uint32_t d) -> const uint32_t* {  // char digit d of window 0 (or any window when whole)
@@ -432,16 +432,43 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
     if (!pl.groups)
       return fail(c, CXBWT_EUNSUPPORTED, "device-memory-bounded slices and parts use the group plan (reads of at most 528 bases)");
     // Figure 2 step 1: suffixes per bucket; then consecutive buckets packed
-    // into slices of at most m1 suffixes.
-    CX_TRY(ensure(c, c->bhist, (uint64_t(1) << kBucketBits) * 8, "bucket counts"));
-    CX_CUDA(c, cudaMemsetAsync(c->bhist.p, 0, (uint64_t(1) << kBucketBits) * 8, st));
-    CX_CUDA(c, launch_bucket_hist(r.R, uint32_t(n), kBucketBits, static_cast<unsigned long long*>(c->bhist.p),
-                                  c->sm_count, st));
-    ++r.launches;
-    std::vector<uint64_t> bh(size_t(1) << kBucketBits);
-    CX_CUDA(c, cudaMemcpyAsync(bh.data(), c->bhist.p, bh.size() * 8, cudaMemcpyDeviceToHost, st));
-    CX_CUDA(c, cudaStreamSynchronize(st));
-    r.d2h += bh.size() * 8;
+    // into slices of at most m1 suffixes.  A build first tries buckets of the
+    // first 4 bases: their counts are sums of the per-position 4-mer counts
+    // (one pass over the bases instead of one per suffix), plus the n
+    // terminator-only suffixes in bucket 0.  When one of them holds more than
+    // a slice, and for parts (whose buckets are 8 bases by definition), the
+    // suffixes are counted per 8-base bucket.
+    std::vector<uint64_t> bh;
+    if (!part) {
+      CX_TRY(ensure(c, c->P, uint64_t(pl.Lmax) * kRadix * 4, "position counts"));
+      CX_CUDA(c, cudaMemsetAsync(c->P.p, 0, uint64_t(pl.Lmax) * kRadix * 4, st));
+      CX_CUDA(c, launch_poscount(r.R, uint32_t(n), pl.Lmax, static_cast<uint32_t*>(c->P.p), c->sm_count, st));
+      ++r.launches;
+      std::vector<uint32_t> P(size_t(pl.Lmax) * kRadix);
+      CX_CUDA(c, cudaMemcpyAsync(P.data(), c->P.p, P.size() * 4, cudaMemcpyDeviceToHost, st));
+      CX_CUDA(c, cudaStreamSynchronize(st));
+      r.d2h += P.size() * 4;
+      std::vector<uint64_t> b4(kRadix, 0);
+      for (uint32_t q = 0; q < pl.Lmax; ++q)
+        for (int v = 0; v < kRadix; ++v) b4[v] += P[size_t(q) * kRadix + v];
+      b4[0] += n;
+      if (*std::max_element(b4.begin(), b4.end()) <= m1) {
+        bh.swap(b4);
+        r.bucket_bits = 8;
+      }
+    }
+    if (bh.empty()) {
+      r.bucket_bits = kBucketBits;
+      CX_TRY(ensure(c, c->bhist, (uint64_t(1) << kBucketBits) * 8, "bucket counts"));
+      CX_CUDA(c, cudaMemsetAsync(c->bhist.p, 0, (uint64_t(1) << kBucketBits) * 8, st));
+      CX_CUDA(c, launch_bucket_hist(r.R, uint32_t(n), kBucketBits, static_cast<unsigned long long*>(c->bhist.p),
+                                    c->sm_count, st));
+      ++r.launches;
+      bh.resize(size_t(1) << kBucketBits);
+      CX_CUDA(c, cudaMemcpyAsync(bh.data(), c->bhist.p, bh.size() * 8, cudaMemcpyDeviceToHost, st));
+      CX_CUDA(c, cudaStreamSynchronize(st));
+      r.d2h += bh.size() * 8;
+    }
     if (counts_only) {
       std::memcpy(part->bucket_counts, bh.data(), bh.size() * 8);
       return CXBWT_OK;
@@ -455,8 +482,8 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
       const bool end = (b == b_hi);
       const uint64_t cnt = end ? 0 : bh[b];
       if (!end && cnt > m1)
-        return fail(c, CXBWT_ENOMEM, "one 8-base bucket holds %llu suffixes, more than the %llu a slice can hold",
-                    (unsigned long long)cnt, (unsigned long long)m1);
+        return fail(c, CXBWT_ENOMEM, "one %u-base bucket holds %llu suffixes, more than the %llu a slice can hold",
+                    r.bucket_bits / 2, (unsigned long long)cnt, (unsigned long long)m1);
       if (end || acc + cnt > m1) {
         if (acc) {
           Slice sl;

@@ -150,7 +150,7 @@ inline uint32_t bits_for(uint32_t x) {  // smallest s with 2^s > x
   return s;
 }
 
-constexpr uint32_t kBucketBits = 16;  // slices are ranges of buckets of the first 8 bases
+constexpr uint32_t kBucketBits = 16;  // parts (and slices when 4-base buckets are too coarse): first 8 bases
 
 struct Plan {
   uint64_t n = 0, sum = 0, N = 0;
@@ -227,6 +227,7 @@ struct Run {
   uint64_t* d_dollar = nullptr;
   uint64_t* d_sa = nullptr;       // global rows
   bool read_major = false;        // multi-slice first pass in read-major order
+  uint32_t bucket_bits = kBucketBits;  // slices are ranges of buckets of the first bucket_bits / 2 bases
   uint64_t launches = 0, sort_launches = 0, sort_items = 0, d2h = 0;
 };
 
