@@ -25,6 +25,8 @@
 // register network, so no group list is materialised for the common case.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "group.cuh"
 
 namespace cxbwt {
@@ -408,11 +410,17 @@ cudaError_t launch_cta_nw(const SegArgs& a, uint32_t grid, const uint2* list, co
                           int dir, uint32_t* work, cudaStream_t st) {
   const size_t smem = size_t(ROWS) * (sizeof(V) + NW * 4 + 2);
   auto kern = k_segsort_cta<NW, V, ROWS, THREADS>;
-  static bool configured = false;  // per instantiation
-  if (!configured) {
-    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  // Set once per instantiation and device (a bit per device; racing threads
+  // set the same value).
+  static std::atomic<unsigned long long> configured{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(configured.load(std::memory_order_acquire) & bit)) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    configured = true;
+    configured.fetch_or(bit, std::memory_order_release);
   }
   kern<<<grid, THREADS, smem, st>>>(a, list, n_ptr, cap, dir, work);
   return cudaGetLastError();

@@ -32,6 +32,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <type_traits>
 
 #include "kernels.cuh"
@@ -365,13 +366,19 @@ template <class V, class S, int MODE, bool WK, bool F>
 cudaError_t launch_mode(const PassArgs& a, cudaStream_t st) {
   const size_t smem = size_t(S::threads) * S::ipt * (sizeof(uint32_t) + sizeof(V));
   auto kern = k_onesweep<V, S::threads, S::ipt, S::min_blocks, MODE, WK, F>;
-  static bool configured = false;  // per instantiation; attributes are per function
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  // Attributes are set once per instantiation and device (a bit per device;
+  // threads that race here both set the same values).
+  static std::atomic<unsigned long long> configured{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(configured.load(std::memory_order_acquire) & bit)) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
-    configured = true;
+    configured.fetch_or(bit, std::memory_order_release);
   }
   kern<<<a.n_tiles, S::threads, smem, st>>>(a);
   return cudaGetLastError();
