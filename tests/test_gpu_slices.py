@@ -1,5 +1,6 @@
 """Device-memory-bounded builds (Figure 2 steps 1-3): the suffixes are split
-into slices of consecutive 8-base buckets that fit the context's budget, each
+into slices of consecutive 4-base buckets (8-base buckets when a 4-base one
+does not fit a slice) that fit the context's budget, each
 slice is sorted and emitted at its global row offset, and the result equals
 the oracle's whatever the number of slices, the id width or the enumeration
 order."""
@@ -63,6 +64,25 @@ def test_uniform_random_slices():
     with binding.Context(device=0, budget_bytes=budget_for(N, 3)) as c:
         assert_same(gpu_bwt(c, codes, lens, want_sa=True), ref, sa=True)
         assert c.stats()["slices"] >= 2
+
+
+def test_slices_from_8_base_buckets():
+    """Reads of 20 bases that all start with AAAA, under a budget of about 14
+    slices: bucket AAAA holds the n terminator-only suffixes and the n whole
+    reads (2/21 of all suffixes), more than a slice, so the planner counts
+    8-base buckets instead, where the largest holds the n terminators alone
+    (1/21)."""
+    _need_gpu()
+    from paper_1401_7457_gb300 import binding
+    codes, lens = synth.uniform_reads(600_000, 20, 64)
+    codes = codes.reshape(-1, 20).copy()
+    codes[:, :4] = 0
+    codes = codes.ravel()
+    ref = oracle_of(codes, lens)
+    N = int(lens.sum()) + lens.size
+    with binding.Context(device=0, budget_bytes=budget_for(N, 14)) as c:
+        assert_same(gpu_bwt(c, codes, lens, want_sa=True), ref, sa=True)
+        assert c.stats()["slices"] >= 11
 
 
 def test_one_bucket_larger_than_a_slice_is_enomem():
