@@ -478,10 +478,11 @@ def run_parts_bench(args, rank, world):
         plan = parts.plan_parts(counts, P)
         per = []
         for p in plan:
-            o = ctx.build_part(w, ln, p.lo, p.hi, p.row0, p.rows)
+            o = ctx.build_part(w, ln, p.lo, p.hi, p.row0, p.rows, bucket_counts=counts)
             for _ in range(max(args.warmup, 1)):
-                ctx.build_part(w, ln, p.lo, p.hi, p.row0, p.rows, *o)
-            per.append(_timed(lambda: ctx.build_part(w, ln, p.lo, p.hi, p.row0, p.rows, *o), args.steps, flush))
+                ctx.build_part(w, ln, p.lo, p.hi, p.row0, p.rows, *o, bucket_counts=counts)
+            per.append(_timed(lambda: ctx.build_part(w, ln, p.lo, p.hi, p.row0, p.rows, *o, bucket_counts=counts),
+                              args.steps, flush))
         res[f"{P}_parts"] = {"part_ms": per, "sum_ms": sum(per), "max_ms": max(per),
                              "rows": [p.rows for p in plan]}
     with tempfile.TemporaryDirectory() as tmp:

@@ -224,6 +224,10 @@ int cxbwt_split_parts(const uint64_t* counts, uint32_t n_buckets, uint32_t n_par
  * bucket_hi), 0 <= bucket_lo < bucket_hi <= CXBWT_BUCKETS.  Its rows are
  * [row0, row0 + rows) of B_R, row0 = the suffixes of the buckets below
  * bucket_lo (both written to *out_row0 and *out_rows, host, may be NULL).
+ *   bucket_counts   host, CXBWT_BUCKETS entries, or NULL: the collection's
+ *                   counts as cxbwt_bucket_counts gives them (a caller that
+ *                   builds several parts passes them to spare a count of
+ *                   every suffix per part); EINVAL when they do not sum to N
  *   out_words       host or device, (row0 % 16 + rows + 15) / 16 words:
  *                   word j holds global BWT word row0 / 16 + j with only the
  *                   part's symbols set (the rest of the first and last word
@@ -236,8 +240,9 @@ int cxbwt_split_parts(const uint64_t* counts, uint32_t n_buckets, uint32_t n_par
  * The caller owns every buffer.  Returns as cxbwt_build; EINVAL for a bad
  * bucket range, EUNSUPPORTED for mixed read lengths. */
 int cxbwt_build_part(cxbwt_ctx* ctx, const uint32_t* reads_2bit, uint64_t n_reads, const uint32_t* lens,
-                     uint32_t bucket_lo, uint32_t bucket_hi, uint32_t* out_words, uint64_t* out_dollar_pos,
-                     uint64_t* out_counts, uint64_t* out_row0, uint64_t* out_rows, void* stream);
+                     uint32_t bucket_lo, uint32_t bucket_hi, const uint64_t* bucket_counts, uint32_t* out_words,
+                     uint64_t* out_dollar_pos, uint64_t* out_counts, uint64_t* out_row0, uint64_t* out_rows,
+                     void* stream);
 
 /* Host only.  ORs a part's words (as cxbwt_build_part writes them, rows
  * [row0, row0 + rows)) into bwt_words, a zero-initialised host buffer of

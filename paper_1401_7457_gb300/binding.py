@@ -74,7 +74,7 @@ SIGNATURES = {
     "cxbwt_autotune": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP, _VP, _VP, _VP]),
     "cxbwt_bucket_counts": (ctypes.c_int, [_VP, _VP, _U64, _VP, _VP, _VP]),
     "cxbwt_split_parts": (ctypes.c_int, [_VP, ctypes.c_uint32, ctypes.c_uint32, _VP, _VP]),
-    "cxbwt_build_part": (ctypes.c_int, [_VP, _VP, _U64, _VP, ctypes.c_uint32, ctypes.c_uint32, _VP, _VP, _VP,
+    "cxbwt_build_part": (ctypes.c_int, [_VP, _VP, _U64, _VP, ctypes.c_uint32, ctypes.c_uint32, _VP, _VP, _VP, _VP,
                                         ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), _VP]),
     "cxbwt_merge_part": (ctypes.c_int, [_VP, _U64, _VP, _U64, _U64]),
     "cxbwt_default_server_options": (None, [_VP]),
@@ -415,11 +415,17 @@ class Context:
         return out
 
     def build_part(self, reads_2bit, lens, bucket_lo: int, bucket_hi: int, row0: int, rows: int,
-                   out_words=None, out_dollar_pos=None, out_counts=None, stream=None):
+                   out_words=None, out_dollar_pos=None, out_counts=None, stream=None, bucket_counts=None):
         """Build the part of B_R of buckets [bucket_lo, bucket_hi), whose rows
-        are [row0, row0 + rows) (from bucket_counts / split_parts).  Missing
+        are [row0, row0 + rows) (from bucket_counts / split_parts; passing
+        those counts spares the device a count of every suffix).  Missing
         outputs are allocated on the inputs' side.  Returns
         ``(words, dollar_pos, counts)``."""
+        bc = None
+        if bucket_counts is not None:
+            bc = np.ascontiguousarray(_to_numpy(bucket_counts), dtype=np.uint64)
+            if bc.size != BUCKETS:
+                raise ValueError(f"bucket_counts needs {BUCKETS} entries")
         n = int(lens.numel() if _is_tensor(lens) else np.asarray(lens).size)
         nw = max(part_words(row0, rows), 1)
         if _is_tensor(reads_2bit) and reads_2bit.is_cuda:
@@ -442,6 +448,7 @@ class Context:
             raise ValueError("out_words holds fewer words than the part needs")
         r0, nr = ctypes.c_uint64(), ctypes.c_uint64()
         _check(lib().cxbwt_build_part(self._h, _ptr(reads_2bit), n, _ptr(lens), bucket_lo, bucket_hi,
+                                      None if bc is None else bc.ctypes.data,
                                       _ptr(out_words), _ptr(out_dollar_pos), _ptr(out_counts), ctypes.byref(r0),
                                       ctypes.byref(nr), _stream_ptr(stream)), self._h)
         if (int(r0.value), int(nr.value)) != (row0, rows):

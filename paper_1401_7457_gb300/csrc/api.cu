@@ -457,6 +457,15 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
         r.bucket_bits = 8;
       }
     }
+    if (bh.empty() && part && part->given_counts) {
+      r.bucket_bits = kBucketBits;
+      bh.assign(part->given_counts, part->given_counts + (size_t(1) << kBucketBits));
+      uint64_t total = 0;
+      for (uint64_t x : bh) total += x;
+      if (total != pl.N)
+        return fail(c, CXBWT_EINVAL, "bucket counts sum to %llu, not the collection's %llu suffixes",
+                    (unsigned long long)total, (unsigned long long)pl.N);
+    }
     if (bh.empty()) {
       r.bucket_bits = kBucketBits;
       CX_TRY(ensure(c, c->bhist, (uint64_t(1) << kBucketBits) * 8, "bucket counts"));
@@ -736,11 +745,13 @@ int cxbwt_split_parts(const uint64_t* counts, uint32_t n_buckets, uint32_t n_par
 }
 
 int cxbwt_build_part(cxbwt_ctx* ctx, const uint32_t* reads_2bit, uint64_t n_reads, const uint32_t* lens,
-                     uint32_t bucket_lo, uint32_t bucket_hi, uint32_t* out_words, uint64_t* out_dollar_pos,
-                     uint64_t* out_counts, uint64_t* out_row0, uint64_t* out_rows, void* stream) {
+                     uint32_t bucket_lo, uint32_t bucket_hi, const uint64_t* bucket_counts, uint32_t* out_words,
+                     uint64_t* out_dollar_pos, uint64_t* out_counts, uint64_t* out_row0, uint64_t* out_rows,
+                     void* stream) {
   PartSpec p;
   p.lo = bucket_lo;
   p.hi = bucket_hi;
+  p.given_counts = bucket_counts;
   p.row0 = out_row0;
   p.rows = out_rows;
   return build_impl(ctx, reads_2bit, n_reads, lens, out_words, out_dollar_pos, out_counts, nullptr, stream, &p);

@@ -206,6 +206,7 @@ struct PartSpec {
   uint32_t lo = 0, hi = 0;
   bool counts_only = false;
   uint64_t* bucket_counts = nullptr;  // host, 2^kBucketBits entries (counts_only)
+  const uint64_t* given_counts = nullptr;  // host, 2^kBucketBits entries, or null: counted on the device
   uint64_t* row0 = nullptr;           // host: the part's first global row
   uint64_t* rows = nullptr;           // host: its number of rows
 };

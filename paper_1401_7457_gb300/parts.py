@@ -69,12 +69,14 @@ def _host(x):
     return binding._to_numpy(x)
 
 
-def build_part_host(ctx, reads_2bit, lens, part: Part, stream=None):
-    """Build one part; its outputs come back as host arrays."""
+def build_part_host(ctx, reads_2bit, lens, part: Part, stream=None, bucket_counts=None):
+    """Build one part; its outputs come back as host arrays.  bucket_counts
+    (the collection's, when the caller has them) spares the device a count."""
     if part.rows == 0:
         n = int(lens.numel() if binding._is_tensor(lens) else np.asarray(lens).size)
         return np.zeros(0, dtype=np.uint32), np.full(n, NO_ROW, dtype=np.uint64), np.zeros(5, dtype=np.uint64)
-    w, d, c = ctx.build_part(reads_2bit, lens, part.lo, part.hi, part.row0, part.rows, stream=stream)
+    w, d, c = ctx.build_part(reads_2bit, lens, part.lo, part.hi, part.row0, part.rows, stream=stream,
+                             bucket_counts=bucket_counts)
     return (_host(w).view(np.uint32)[: binding.part_words(part.row0, part.rows)], _host(d).view(np.uint64),
             _host(c).view(np.uint64))
 
@@ -111,7 +113,7 @@ def build_sharded(ctx, reads_2bit, lens, group=None, stream=None):
     parts = plan_parts(counts, world)
     n_symbols = int(counts.sum())
     n_reads = int(lens.numel() if binding._is_tensor(lens) else np.asarray(lens).size)
-    local = build_part_host(ctx, reads_2bit, lens, parts[rank], stream=stream)
+    local = build_part_host(ctx, reads_2bit, lens, parts[rank], stream=stream, bucket_counts=counts)
     return gather_parts(local, parts[rank], n_symbols, n_reads, group=group)
 
 
@@ -149,7 +151,7 @@ def build_rounds(ctx, reads_2bit, lens, n_rounds: int, out_dir: str, stop_after:
     bucket_counts = np.asarray(bucket_counts, dtype=np.uint64)
     if builder is None:
         def builder(p):
-            return build_part_host(ctx, reads_2bit, lens, p)
+            return build_part_host(ctx, reads_2bit, lens, p, bucket_counts=bucket_counts)
     parts = plan_parts(bucket_counts, n_rounds)
     n_symbols = int(bucket_counts.sum())
     n_words = (n_symbols + 15) // 16

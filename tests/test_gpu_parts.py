@@ -68,7 +68,9 @@ def test_parts_merge_to_oracle(ctx, n_parts, where):  # noqa: F811
     res = parts.empty_result(len(ref["bwt"]), lens.size)
     plan = parts.plan_parts(counts, n_parts)
     for p in plan:
-        parts.merge_into(res, p, *parts.build_part_host(ctx, words, lens_in, p))
+        # Half the parts take the counts from the caller, half count again.
+        given = counts if p.lo % 2 == 0 else None
+        parts.merge_into(res, p, *parts.build_part_host(ctx, words, lens_in, p, bucket_counts=given))
     torch.cuda.synchronize()
     assert np.array_equal(res[0], _words(ref["bwt"]))
     assert np.array_equal(res[1], ref["dollar_pos"])
@@ -125,3 +127,14 @@ def test_part_rejects_bad_ranges_and_mixed_lengths(ctx):  # noqa: F811
     with pytest.raises(binding.CxbwtError) as e:
         ctx.bucket_counts(binding.pack_codes(codes2), lens2)
     assert e.value.status == -5
+
+
+def test_part_rejects_counts_of_another_collection(ctx):  # noqa: F811
+    from paper_1401_7457_gb300 import binding
+    codes, lens = _collection(2000, 100, 61)
+    words = binding.pack_codes(codes)
+    counts = ctx.bucket_counts(words, lens)
+    counts[5] += 1
+    with pytest.raises(binding.CxbwtError) as e:
+        ctx.build_part(words, lens, 0, 65536, 0, int(counts.sum()) - 1, bucket_counts=counts)
+    assert e.value.status == -1
