@@ -4,10 +4,13 @@
 // A build sorts one or more "slices" of the suffixes and emits each slice's
 // part of the BWT at its global row offset.  A slice is the whole collection
 // when its workspace fits the device budget; otherwise the planner of Figure
-// 2 steps 1-3 applies: one scan counts the suffixes of every bucket (first 8
-// bases), consecutive buckets are packed into slices of at most m1 suffixes
-// (m1 from the budget), and each slice rescans all suffixes keeping those of
-// its buckets (the listing of step 3(a)).  Per slice, on the caller's stream:
+// 2 steps 1-3 applies: the suffixes of every bucket are counted (first 4
+// bases, summed from the per-position 4-mer counts; first 8 bases, one count
+// per suffix, when a 4-base bucket is larger than a slice, and always for a
+// bucket-range part), consecutive buckets are packed into slices of at most
+// m1 suffixes (m1 from the budget), and each slice rescans all suffixes
+// keeping those of its buckets (the listing of step 3(a)).  Per slice, on the
+// caller's stream:
 //   1. digit histograms: k_poscount + k_digitbase (whole collection) or
 //      k_pass_hist (the slice's buckets) - the first output row of every digit
 //      value of every pass;
@@ -19,9 +22,10 @@
 //      first, each 16-base stringword window gathered once and carried in the
 //      key array for its remaining passes - every window (LSD plan) or only
 //      the first (group plan, followed by the on-chip group finish);
-//   4. emission (Figure 2 step 3(c)(iii)); with host outputs, the finished
-//      words of each slice stream to the host on a side stream while the
-//      next slice sorts.
+//   4. emission (Figure 2 step 3(c)(iii)), with the preceding base carried
+//      in the ids when the store is out of L2; with host outputs, the
+//      finished words of each slice stream to the host on a side stream while
+//      the next slice sorts.
 #include "host.cuh"
 
 using namespace cxbwt;
