@@ -642,6 +642,11 @@ def main():
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"first {min(args.cpu_sample_reads, n):,} reads ({sb:,} bases) of the workload, "
                          f"{dt:.1f} s wall"}
+        # The same oracle on one core, on a smaller sample (a few seconds).
+        n1 = max(1, args.cpu_sample_reads // 5)
+        rate1, dt1, sb1 = cpu_oracle_rate(codes, lens, n1, 1)
+        cpu["single_thread"] = {"value": rate1, "unit": UNIT, "cores": 1,
+                                "sample": f"first {min(n1, n):,} reads ({sb1:,} bases), {dt1:.1f} s wall"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
