@@ -84,8 +84,9 @@ __device__ __forceinline__ uint32_t window16(const ReadIndex& R, const Suffix& s
   const uint32_t sh = uint32_t(q & 15u) * 2u;
   uint32_t first, next;
   const uint32_t o = uint32_t(w & 3u);
-  if (R.words_aligned && o < 3 && w + 1 < R.n_words) {
-    // Both words sit in one aligned 16-byte chunk: one load.
+  if (R.words_aligned && o < 3 && (w | 3u) < R.n_words) {
+    // Both words sit in one aligned 16-byte chunk that lies wholly inside the
+    // store: one load.
     const uint4 c = __ldg(reinterpret_cast<const uint4*>(R.words) + (w >> 2));
     first = o == 0 ? c.x : o == 1 ? c.y : c.z;
     next = o == 0 ? c.y : o == 1 ? c.z : c.w;
