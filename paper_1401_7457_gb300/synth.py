@@ -114,8 +114,8 @@ def sample_reads(genome: np.ndarray, n: int, length: int, seed: int, sub_rate: f
 
 
 # ---------------------------------------------------------------------------
-# The five workloads.  Sizes follow the paper's 100 bp reads; see the design doc
-# for the recipe of each.
+# The five workloads.  Sizes follow the paper's 100 bp reads; each function
+# below states its recipe.
 # ---------------------------------------------------------------------------
 
 def tiny_uniform(seed: int = 1):
