@@ -76,3 +76,35 @@ def test_output_size(lib):
 def test_status_strings(lib):
     lib.cxbwt_status_string.restype = ctypes.c_char_p
     assert lib.cxbwt_status_string(-4) == b"CXBWT_ETIMEOUT"
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets
+    that the C compiler gives the header's struct (a mismatch would pass
+    garbage through the ABI without an error)."""
+    import shutil
+    import subprocess
+
+    from paper_1401_7457_gb300 import binding
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    structs = {"cxbwt_options": binding.Options, "cxbwt_stats": binding.Stats, "cxbwt_tuning": binding.Tuning,
+               "cxbwt_server_options": binding.ServerOptions, "cxbwt_request": binding.Request,
+               "cxbwt_collection": binding.Collection}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "cxbwt.h"', "int main(void) {"]
+    want = []
+    for cname, py in structs.items():
+        lines.append(f'  printf("%zu\\n", sizeof({cname}));')
+        want.append(ctypes.sizeof(py))
+        for fname, _ in py._fields_:
+            field = getattr(py, fname)
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {fname.rstrip("_")}));')
+            want.append(field.offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == want
