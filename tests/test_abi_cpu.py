@@ -108,3 +108,23 @@ def test_binding_structs_match_the_header(tmp_path):
     subprocess.run([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
     assert got == want
+
+
+def test_binding_signatures_match_the_header():
+    """Each entry point's ctypes signature takes as many arguments as its C
+    prototype, and returns a value exactly when the prototype does."""
+    from paper_1401_7457_gb300 import binding
+    protos = {}
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            for ret, name, params in re.findall(r"([\w\s\*]+?)\b(cxbwt_\w+)\s*\(([^)]*)\)\s*;", text):
+                params = params.strip()
+                n = 0 if params in ("", "void") else params.count(",") + 1
+                protos[name] = (ret.split()[-1] != "void" or "*" in ret, n)
+    assert set(protos) == set(binding.SIGNATURES)
+    for name, (returns, n) in protos.items():
+        restype, argtypes = binding.SIGNATURES[name]
+        assert len(argtypes) == n, name
+        assert (restype is not None) == returns, name
