@@ -10,7 +10,8 @@ L2 flushed by a 512 MB write between steps, outside the timed events).
 Extra keys: ``e2e`` (same metric through the C ABI with pinned host buffers,
 copies inside the timed region), ``roofline`` of the dominant kernel (the
 onesweep digit pass, 16 algorithmic bytes per suffix per pass, timed live
-with the library's own CUDA events), ``cpu_baseline`` (the oracle on a bounded
+with the library's own CUDA events), ``phases`` (every phase of a build
+against its own algorithmic bytes), ``cpu_baseline`` (the oracle on a bounded
 sample on this host's cores, rank 0 only), ``clocks`` (nvidia-smi sampled
 during the timed region) and ``gpu_launches``.
 
@@ -61,6 +62,8 @@ def load_workload(name, rank=0, n_reads=0):
         seed = 1 if rank == 0 else synth.derive_seed(1, rank)
         codes, lens = synth.uniform_reads(n_reads or 10_000, 100, seed)
     return WORKLOADS[name], codes, lens
+
+
 PROFILE = os.path.join(ROOT, "profiles", "onesweep_digit_pass_genome_like.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_1401_7457_gb300", "csrc", "onesweep.cuh")
 FALLBACK_HBM_GBS = 6800.0
@@ -173,6 +176,39 @@ def aggregate(dist, local_ms, bases_per_rank, world, steps):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total = float(t.item())
     return bases_per_rank * world * steps / (total * 1e-3) / 1e9, total
+
+
+def phase_rates(st, steps, n_reads, bases, idb, peak):
+    """Device time of each phase of one build and its bandwidth against the
+    phase's own algorithmic bytes (N = bases + n_reads suffixes, idb = bytes
+    of a suffix id):
+
+    * digit passes: key (4 B) and id read and written, per item of each pass;
+    * group finish: the window key and the id of every suffix read, the id
+      written;
+    * emission: the id of every suffix read, its 2-bit symbol written, 8 B per
+      $ row, the read store (a quarter byte per base) read once;
+    * histograms and planning (the rest of the build): the read store and the
+      read lengths read once.
+
+    st holds the library's counters over `steps` builds (timing enabled).  A
+    phase that did not run (no time) is left out."""
+    N = bases + n_reads
+    sort_ms = st["sort_pass_ms"] / steps
+    group_ms = st["group_ms"] / steps
+    emit_ms = st["emit_ms"] / steps
+    rest_ms = st["build_ms"] / steps - sort_ms - group_ms - emit_ms
+    model = {"digit_passes": (sort_ms, (8 + 2 * idb) * st["sort_pass_items"] / steps),
+             "group_finish": (group_ms, (4 + 2 * idb) * N),
+             "emission": (emit_ms, idb * N + N / 4 + 8 * n_reads + bases / 4),
+             "histograms_and_planning": (rest_ms, bases / 4 + 4 * n_reads)}
+    out = {}
+    for name, (ms, nbytes) in model.items():
+        if ms <= 0:
+            continue
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[name] = {"ms_per_step": ms, "bytes_per_step": nbytes, "gbs": gbs, "frac_of_hbm": gbs / peak}
+    return out
 
 
 def cpu_oracle_rate(codes, lens, n_sample_reads, threads):
@@ -655,7 +691,8 @@ def main():
                 "config": {"workload": desc.format(n=n, N=N), "n_reads": n, "read_len": int(lens[0]), "bases_per_gpu": bases,
                            "suffixes_per_gpu": N, "l2": "flushed between steps (512 MB write outside the events)",
                            "input": "device-resident (HBM) before the timed region; outputs left in HBM"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "phases": phase_rates(st, args.steps, n, bases, idb, peak),
+                "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(st["kernel_launches"]), "gpu_launches_per_step": launches_per_step,
                 "clocks": clocks.summary(),
                 "detail": {"step_ms": ms, "slices_per_step": st["slices"] / args.steps,

@@ -46,3 +46,25 @@ def test_reference_arm_other_ranks_do_no_work():
     with redirect_stdout(buf):
         rc = bench.run_reference(args, rank=1, world=2)
     assert rc == 0 and buf.getvalue() == ""
+
+
+def test_phase_rates_against_each_phase_bytes():
+    """The per-phase figures of the benchmark line, from the library's
+    counters over two builds of 1M reads x 100 bp with 32-bit ids."""
+    import bench
+    n, bases, steps = 1_000_000, 100_000_000, 2
+    N = n + bases
+    st = {"sort_pass_ms": 2 * 2.61, "group_ms": 2 * 1.69, "emit_ms": 2 * 0.37, "build_ms": 2 * 4.84,
+          "sort_pass_items": 2 * 4 * N}
+    ph = bench.phase_rates(st, steps, n, bases, 4, 6792.0)
+    assert set(ph) == {"digit_passes", "group_finish", "emission", "histograms_and_planning"}
+    assert abs(ph["digit_passes"]["bytes_per_step"] - 16 * 4 * N) < 1
+    assert abs(ph["digit_passes"]["gbs"] - 16 * 4 * N / 2.61e-3 / 1e9) < 1e-6
+    assert abs(ph["group_finish"]["bytes_per_step"] - 12 * N) < 1
+    assert abs(ph["emission"]["bytes_per_step"] - (4 * N + N / 4 + 8 * n + bases / 4)) < 1
+    assert abs(ph["histograms_and_planning"]["ms_per_step"] - (4.84 - 2.61 - 1.69 - 0.37)) < 1e-9
+    for v in ph.values():
+        assert abs(v["frac_of_hbm"] - v["gbs"] / 6792.0) < 1e-12
+    # A plan without a group finish (every digit by LSD passes) reports no such phase.
+    st["group_ms"] = 0.0
+    assert "group_finish" not in bench.phase_rates(st, steps, n, bases, 4, 6792.0)
