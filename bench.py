@@ -113,29 +113,96 @@ def profiled_traffic():
     return float(m.group(1))
 
 
-class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+# Clock-event reason bits of NVML (nvml.h), under the names nvidia-smi uses.
+NVML_REASONS = {"hw_slowdown": 0x8 | 0x80, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20,
+                "sw_power_cap": 0x4}
+NVML_CLOCK_SM = 1
 
-    def __init__(self, index: int):
-        self.index = index
+
+def summarize_clocks(rows, source):
+    """rows: (sm_mhz, sm_max_mhz, reasons) samples; reasons a set of names."""
+    if not rows:
+        return None
+    return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+            "samples": len(rows), "reasons": sorted(set().union(*(r[2] for r in rows))), "source": source}
+
+
+class ClockSampler:
+    """SM clock and clock-event reasons during a timed region.  NVML is read
+    (read-only queries) from a thread every 5 ms; where NVML cannot be loaded,
+    nvidia-smi samples every 200 ms (too coarse for a region of a few tens
+    of milliseconds, hence NVML first)."""
+
+    def __init__(self, gpu, period_s: float = 0.005):
+        self.gpu = gpu  # NVML / nvidia-smi id: a PCI bus id string, or an index
+        self.period = period_s
+        self.rows = []
+        self.source = None
         self.proc = None
         self.path = None
+        self.thread = None
 
     def __enter__(self):
+        if not self._start_nvml():
+            self._start_smi()
+        return self
+
+    def _start_nvml(self):
+        import ctypes
+        import threading
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            reasons = (getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+                       or lib.nvmlDeviceGetCurrentClocksThrottleReasons)
+            if lib.nvmlInit_v2() != 0:
+                return False
+            h = ctypes.c_void_p()
+            mx = ctypes.c_uint()
+            if isinstance(self.gpu, str):
+                found = lib.nvmlDeviceGetHandleByPciBusId_v2(self.gpu.encode(), ctypes.byref(h))
+            else:
+                found = lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.gpu), ctypes.byref(h))
+            if found != 0 or lib.nvmlDeviceGetMaxClockInfo(h, NVML_CLOCK_SM, ctypes.byref(mx)) != 0:
+                lib.nvmlShutdown()
+                return False
+        except (OSError, AttributeError):
+            return False
+        self.lib = lib
+        self.stop = threading.Event()
+
+        def loop():
+            clk, r = ctypes.c_uint(), ctypes.c_ulonglong()
+            while not self.stop.is_set():
+                if (lib.nvmlDeviceGetClockInfo(h, NVML_CLOCK_SM, ctypes.byref(clk)) == 0
+                        and reasons(h, ctypes.byref(r)) == 0):
+                    names = {k for k, bits in NVML_REASONS.items() if r.value & bits}
+                    self.rows.append((float(clk.value), float(mx.value), names))
+                self.stop.wait(self.period)
+
+        self.source = f"nvml every {self.period * 1e3:g} ms"
+        self.thread = threading.Thread(target=loop, daemon=True)
+        self.thread.start()
+        return True
+
+    def _start_smi(self):
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            self.source = "nvidia-smi every 200 ms"
         except Exception:
             self.proc = None
-        return self
 
     def __exit__(self, *exc):
+        if self.thread:
+            self.stop.set()
+            self.thread.join()
+            self.lib.nvmlShutdown()
         if self.proc:
             self.proc.terminate()
             try:
@@ -144,24 +211,35 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
+        if self.thread:
+            return summarize_clocks(self.rows, self.source)
         if not self.proc or not self.path:
             return None
         rows = []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in open(self.path):
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
             try:
-                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                flags = {names[i] for i, f in enumerate(parts[5:9]) if f.lower().startswith("active")}
+                rows.append((float(parts[1]), float(parts[2]), flags))
             except ValueError:
                 continue
         os.unlink(self.path)
-        if not rows:
-            return None
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for _, _, flags in rows for i, f in enumerate(flags) if f.lower().startswith("active")})
-        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "samples": len(rows), "reasons": reasons}
+        return summarize_clocks(rows, self.source)
+
+
+def nvml_id(dev):
+    """The GPU's PCI bus id, as NVML and nvidia-smi name it (their indices
+    differ from CUDA's when CUDA_VISIBLE_DEVICES is set), or the CUDA index
+    when torch does not report the bus."""
+    import torch
+    p = torch.cuda.get_device_properties(dev)
+    try:
+        return f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+    except AttributeError:
+        return dev.index
 
 
 def aggregate(dist, local_ms, bases_per_rank, world, steps):
@@ -609,7 +687,7 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clocks:
+    with ClockSampler(nvml_id(dev)) as clocks:
         for i in range(args.steps):
             flush.fill_(i & 0xFF)  # evict the previous step's data from L2 (outside the events)
             ev[i][0].record(stream)

@@ -68,3 +68,72 @@ def test_phase_rates_against_each_phase_bytes():
     # A plan without a group finish (every digit by LSD passes) reports no such phase.
     st["group_ms"] = 0.0
     assert "group_finish" not in bench.phase_rates(st, steps, n, bases, 4, 6792.0)
+
+
+class _FakeNvml:
+    """Answers the read-only NVML queries the clock sampler makes."""
+
+    def __init__(self):
+        self.shutdown = 0
+
+    def nvmlInit_v2(self):
+        return 0
+
+    def nvmlShutdown(self):
+        self.shutdown += 1
+        return 0
+
+    def nvmlDeviceGetHandleByPciBusId_v2(self, bus, handle):
+        self.bus = bus
+        return 0
+
+    def nvmlDeviceGetMaxClockInfo(self, handle, kind, out):
+        out._obj.value = 2070
+        return 0
+
+    def nvmlDeviceGetClockInfo(self, handle, kind, out):
+        out._obj.value = 1965
+        return 0
+
+    def nvmlDeviceGetCurrentClocksEventReasons(self, handle, out):
+        out._obj.value = 0x4 | 0x1  # power cap, idle (not reported)
+        return 0
+
+
+def test_clock_sampler_reads_nvml(monkeypatch):
+    import ctypes
+    import time
+
+    import bench
+    fake = _FakeNvml()
+    monkeypatch.setattr(ctypes, "CDLL", lambda name: fake)
+    with bench.ClockSampler("00000000:1B:00.0", period_s=0.001) as c:
+        time.sleep(0.05)
+    s = c.summary()
+    assert fake.shutdown == 1 and fake.bus == b"00000000:1B:00.0"
+    assert s["samples"] >= 5 and s["sm_mhz"] == 1965 and s["sm_max_mhz"] == 2070
+    assert s["reasons"] == ["sw_power_cap"] and s["source"].startswith("nvml")
+
+
+def test_clock_sampler_without_nvml_or_smi(monkeypatch):
+    """No NVML library and no nvidia-smi (this host): no record, no error."""
+    import ctypes
+
+    import bench
+
+    def missing(name):
+        raise OSError(name)
+
+    monkeypatch.setattr(ctypes, "CDLL", missing)
+    monkeypatch.setenv("PATH", "/nonexistent")
+    with bench.ClockSampler(0) as c:
+        pass
+    assert c.summary() is None
+
+
+def test_summarize_clocks():
+    import bench
+    rows = [(2070.0, 2070.0, set()), (1900.0, 2070.0, {"sw_power_cap"}), (2000.0, 2070.0, set())]
+    s = bench.summarize_clocks(rows, "x")
+    assert s == {"sm_mhz": 2000.0, "sm_max_mhz": 2070.0, "samples": 3, "reasons": ["sw_power_cap"], "source": "x"}
+    assert bench.summarize_clocks([], "x") is None
