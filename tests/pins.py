@@ -9,6 +9,9 @@ Each check is independent of ``oracle/cx_oracle.cpp``:
   or before the first marker, which is exactly the order of Section 2.  Python
   list comparison does the sorting; nothing is shared with the oracle's
   comparator.
+* ``rotation_rows`` - the same rotation sort, returning the suffix of each
+  row: pins the oracle's rank and sortedness certificate (the two checks the
+  GPU tests use at sizes the full sort cannot reach).
 * worked examples (Figure 1) and hand-derived cases under ``tests/golden/``.
 * closed forms: one read is the plain BWT of S$; n identical reads repeat each
   symbol of that BWT n times.
@@ -44,6 +47,22 @@ def rotation_bwt(reads):
         prev = T[p - 1]  # cyclic: T[-1] is $_{n-1}
         out.append("$" if prev < n else "ACGT"[prev - n])
     return "".join(out)
+
+
+def rotation_rows(reads):
+    """(read, offset) of each rotation of the same concatenation, in sorted
+    order: the suffix order of Section 2 by brute force (offset L_i names the
+    rotation starting at $_i, the terminator-only suffix)."""
+    n = len(reads)
+    T, where = [], []
+    for i, r in enumerate(reads):
+        for k, c in enumerate(r):
+            T.append(n + "ACGT".index(c))
+            where.append((i, k))
+        T.append(i)
+        where.append((i, len(r)))
+    rots = sorted(range(len(T)), key=lambda p: T[p:] + T[:p])
+    return [where[p] for p in rots]
 
 
 def read_figure1():
@@ -197,4 +216,21 @@ def run_all_pins(lib=None, n_random=300, seed=7):
         check_invariants(codes, lens, res["bwt"], res["dollar_pos"], res["counts"])
     except AssertionError:
         failed.append("invariants")
+    # Rank and certificate against the brute-force order of all rotations:
+    # the rank of the suffix in row r is r, the rotation order passes the
+    # certificate, and a swap of the first or the last two rows fails it there.
+    reads = ["ACGTTG", "ACG", "TTGA", "ACGTTG", "G"]
+    rows = rotation_rows(reads)
+    col = oracle.Collection.from_strings(reads)
+    sa_r = np.array([i for i, _ in rows], dtype=np.uint64)
+    sa_p = np.array([k for _, k in rows], dtype=np.uint32)
+    N = len(rows)
+    ok = all(oracle.rank(col, i, k, lib=lib) == r for r, (i, k) in enumerate(rows))
+    ok = ok and oracle.check_sa(col, sa_r, sa_p, lib=lib) == -1
+    for a in (0, N - 2):
+        sr, sp = sa_r.copy(), sa_p.copy()
+        sr[[a, a + 1]], sp[[a, a + 1]] = sr[[a + 1, a]], sp[[a + 1, a]]
+        ok = ok and oracle.check_sa(col, sr, sp, lib=lib) == a
+    if not ok:
+        failed.append("rank_and_certificate")
     return failed

@@ -23,6 +23,9 @@ MUTANTS = {
                                  "const uint32_t m = la < lb ? (la ? la - 1 : 0) : (lb ? lb - 1 : 0);"),
     "preceding_symbol_off_by_one": ("seq[off[s.read] + s.pos - 1]", "seq[off[s.read] + s.pos]"),
     "dollar_at_wrong_end": ("s.pos == 0 ? '$'", "s.pos == len[s.read] ? '$'"),
+    "rank_counts_equal_suffix": ("if (suffix_less(R, Suffix{uint64_t(i), k}, q)) ++count;",
+                                 "if (!suffix_less(R, q, Suffix{uint64_t(i), k})) ++count;"),
+    "certificate_skips_last_pair": ("for (int64_t r = 0; r < last; ++r) {", "for (int64_t r = 0; r < last - 1; ++r) {"),
 }
 
 RUNNER = r"""
