@@ -76,7 +76,7 @@ def test_mixed_lengths(ctx, lo, hi, n):
 
 
 @pytest.mark.parametrize("case", ["one_base", "one_read", "all_a", "all_t", "identical", "two_letters",
-                                  "tile_exact", "long_read"])
+                                  "tile_exact", "long_read", "max_len_read"])
 def test_edge_cases(ctx, case):
     rng = np.random.default_rng(5)
     if case == "one_base":
@@ -96,8 +96,11 @@ def test_edge_cases(ctx, case):
     elif case == "tile_exact":  # N = 2 * 4096 exactly: no ragged tile
         codes, lens = synth.uniform_reads(128, 63, 3)
         assert int(lens.sum()) + lens.size == 8192
-    else:  # one 20,000-base read plus short ones
+    elif case == "long_read":  # one 20,000-base read plus short ones
         lens = np.array([20_000] + [30] * 100, dtype=np.uint32)
+        codes = rng.integers(0, 4, size=int(lens.sum())).astype(np.uint8)
+    else:  # the longest read the ABI accepts (65,535 bases) plus short ones
+        lens = np.array([30] * 50 + [65_535] + [30] * 50, dtype=np.uint32)
         codes = rng.integers(0, 4, size=int(lens.sum())).astype(np.uint8)
     assert_same(gpu_bwt(ctx, codes, lens, want_sa=True), oracle_of(codes, lens), sa=True)
 
