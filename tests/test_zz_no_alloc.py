@@ -45,6 +45,30 @@ def test_noalloc_equals_build_on_consecutive_calls():
             assert torch.equal(rc, c), "counts differ from cxbwt_build"
 
 
+@pytest.mark.parametrize("L,n", [(255, 8192), (272, 7681)])
+def test_noalloc_at_its_limits(L, n):
+    """Exactly CXBWT_NOALLOC_MAX_SUFFIXES suffixes (8192 reads x 255 bases),
+    and the longest read length it takes (272 bases): the oracle's result,
+    and the same words as cxbwt_build."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    from paper_1401_7457_gb300 import binding
+    codes, lens = synth.uniform_reads(n, L, 74 + L)
+    N = n * (L + 1)
+    assert N <= binding.NOALLOC_MAX_SUFFIXES and L <= binding.NOALLOC_MAX_READ_LEN
+    if L == 255:
+        assert N == binding.NOALLOC_MAX_SUFFIXES
+    ref = oracle.bwt(oracle.Collection(codes, lens), threads=8)
+    with binding.Context(device=0) as ctx:
+        (rb, rd, rc), (b, d, c) = _both(ctx, codes, lens)
+    assert torch.equal(rb, b) and torch.equal(rd, d) and torch.equal(rc, c)
+    dpos = d.cpu().numpy().view(np.uint64)
+    assert binding.unpack_ascii(b.cpu().numpy().view(np.uint32), dpos, N) == ref["bwt"]
+    assert np.array_equal(dpos, ref["dollar_pos"])
+    assert np.array_equal(c.cpu().numpy().view(np.uint64), ref["counts"])
+
+
 def test_noalloc_rejects_sizes_beyond_its_limit():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
