@@ -81,7 +81,7 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
   int cur = 0, kin = 0;
   const int idb = pl.idb;
   bool first = pl.uniform;  // the first digit pass generates the start order
-  a.n_gen = sl.whole ? pl.N : pl.N;  // generated passes enumerate every suffix
+  a.n_gen = pl.N;  // generated passes enumerate every suffix (a slice's pass filters them)
   a.n_out = sl.rows;
   a.n_tiles = uint32_t((pl.N + TILE - 1) / TILE);
   if (!pl.uniform) {
