@@ -1,6 +1,7 @@
-// BWT emission: Figure 2 step 3(c)(iii) of the paper ("for each suffix in the
-// sorted order, output its preceding character"), with the Section 2 rule
-// that a suffix starting at position 0 is preceded by $.
+// BWT emission: Figure 2 step 3(c)(iii) of the paper, where the suffixes are
+// walked in sorted order and each one contributes the base just before it to
+// the BWT, with the Section 2 rule that a suffix starting at position 0 is
+// preceded by $.
 //
 // Each thread owns one packed output word (16 consecutive global rows), so it
 // assembles the word by itself: up to 16 sorted ids, the preceding base of
