@@ -65,6 +65,33 @@ def rotation_rows(reads):
     return [where[p] for p in rots]
 
 
+def result_digest(bwt_ascii: bytes, dollar_pos, counts) -> str:
+    """SHA-256 of a result: the ASCII BWT, then the $ rows and the five counts
+    as little-endian uint64."""
+    import hashlib
+    h = hashlib.sha256()
+    h.update(bytes(bwt_ascii))
+    h.update(np.ascontiguousarray(dollar_pos, dtype="<u8").tobytes())
+    h.update(np.ascontiguousarray(counts, dtype="<u8").tobytes())
+    return h.hexdigest()
+
+
+def input_digest(codes, lens) -> str:
+    """SHA-256 of a collection: its base codes (uint8), then its lengths as
+    little-endian uint32."""
+    import hashlib
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(codes, dtype=np.uint8).tobytes())
+    h.update(np.ascontiguousarray(lens, dtype="<u4").tobytes())
+    return h.hexdigest()
+
+
+def read_oracle_digests():
+    import json
+    with open(os.path.join(GOLDEN, "oracle_digests.json")) as f:
+        return json.load(f)
+
+
 def read_figure1():
     with open(os.path.join(GOLDEN, "figure1.txt")) as f:
         rows = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]

@@ -1,5 +1,6 @@
 """Pins of the CPU oracle against the paper and the mathematics (no GPU)."""
 import itertools
+import os
 
 import numpy as np
 import pytest
@@ -123,3 +124,21 @@ def test_tiny_uniform_workload_invariants():
     res = oracle.bwt(col)
     assert col.n_suffixes == 1_010_000
     pins.check_invariants(codes, lens, res["bwt"], res["dollar_pos"], res["counts"])
+
+
+def test_oracle_reproduces_its_stored_digest():
+    """The oracle's result for the 10,000 x 100 bp workload has the digest
+    that tests/golden/make_oracle_digests.py stored (the GPU tests compare
+    with the stored digests)."""
+    want = pins.read_oracle_digests()["tiny"]
+    codes, lens = synth.tiny_uniform()
+    assert pins.input_digest(codes, lens) == want["input_sha256"]
+    res = oracle.bwt(oracle.Collection(codes, lens), threads=os.cpu_count() or 1)
+    assert len(res["bwt"]) == want["n_symbols"]
+    assert pins.result_digest(res["bwt"], res["dollar_pos"], res["counts"]) == want["sha256"]
+    # Each part of a result enters the digest.
+    flipped = bytearray(res["bwt"])
+    flipped[5] = ord("A") if flipped[5] != ord("A") else ord("C")
+    assert pins.result_digest(bytes(flipped), res["dollar_pos"], res["counts"]) != want["sha256"]
+    assert pins.result_digest(res["bwt"], res["dollar_pos"] + np.uint64(1), res["counts"]) != want["sha256"]
+    assert pins.result_digest(res["bwt"], res["dollar_pos"], res["counts"][::-1]) != want["sha256"]
