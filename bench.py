@@ -289,6 +289,26 @@ def phase_rates(st, steps, n_reads, bases, idb, peak):
     return out
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
 def cpu_oracle_rate(codes, lens, n_sample_reads, threads):
     """Oracle throughput on the first n_sample_reads reads: (Gbase/s, seconds, bases)."""
     import oracle
@@ -326,7 +346,8 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic", "config": {"workload": desc.format(n=lens.size, N=int(lens.sum()) + lens.size)},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "cpu_model": cpu_model(), "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -753,7 +774,7 @@ def main():
         oracle.build()
         threads = os.cpu_count() or 1
         rate, dt, sb = cpu_oracle_rate(codes, lens, args.cpu_sample_reads, threads)
-        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "cpu_model": cpu_model(), "kind": "oracle",
                "sample": f"first {min(args.cpu_sample_reads, n):,} reads ({sb:,} bases) of the workload, "
                          f"{dt:.1f} s wall"}
         # The same oracle on one core, on a smaller sample (a few seconds).

@@ -34,6 +34,7 @@ def test_reference_arm_json_line():
     cpu = line["cpu_baseline"]
     assert cpu["kind"] == "oracle" and cpu["value"] == line["value"] and cpu["unit"] == line["unit"]
     assert cpu["cores"] >= 1 and "2,000 reads" in cpu["sample"]
+    assert isinstance(cpu["cpu_model"], str) and cpu["cpu_model"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
 
