@@ -218,3 +218,61 @@ def test_rounds_resume_after_interruption(tmp_path):
 def test_rounds_for_host_budget():
     assert parts.rounds_for_host_budget(1000, 1 << 20) == 1
     assert parts.rounds_for_host_budget(4_000_000, 250_000) == 4
+
+
+class OracleContext:
+    """Stands in for a device context on CPU ranks: the bucket counts and
+    each part's outputs come from the oracle (cut by oracle_part)."""
+
+    def __init__(self, codes, lens):
+        self.codes, self.lens = codes, lens
+        self.ref = oracle.bwt(oracle.Collection(codes, lens))
+        self.given = []
+
+    def bucket_counts(self, reads_2bit, lens, stream=None):
+        return bucket_counts(self.codes, self.lens)
+
+    def build_part(self, reads_2bit, lens, lo, hi, row0, rows, stream=None, bucket_counts=None):
+        self.given.append(bucket_counts is not None)
+        return oracle_part(self.ref, self.lens.size, parts.Part(lo, hi, row0, rows))
+
+
+def _rank_sharded(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import torch.distributed as dist
+
+    import test_parts_cpu as T
+    from paper_1401_7457_gb300 import parts as P
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    codes, lens = T.small_collection(seed=31, n=400)
+    ctx = T.OracleContext(codes, lens)
+    out = P.build_sharded(ctx, T.binding.pack_codes(codes), lens)
+    if rank == 0:
+        ok = (np.array_equal(out[0], T.whole_words(ctx.ref["bwt"])) and np.array_equal(out[1], ctx.ref["dollar_pos"])
+              and np.array_equal(out[2], ctx.ref["counts"]))
+        q.put(("merged", ok, ctx.given))
+    else:
+        q.put(("rank", out is None, ctx.given))
+    dist.destroy_process_group()
+
+
+def test_two_ranks_build_sharded():
+    """parts.build_sharded on two gloo ranks: each rank counts the buckets,
+    builds its own part with those counts, and rank 0 gets the whole B_R."""
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_sharded, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    d = {k: (v, given) for k, v, given in got}
+    assert d["merged"][0], "rank 0's merged B_R differs from the oracle"
+    assert d["rank"][0], "rank 1 must get None"
+    assert d["merged"][1] == [True] and d["rank"][1] == [True], "each rank builds one part with the counts"
