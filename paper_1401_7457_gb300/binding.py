@@ -125,6 +125,8 @@ class Server:
 
     def submit(self, reads_2bit, lens, out_bwt, out_dollar_pos=None, out_counts=None) -> int:
         """Queue a request (host arrays, kept alive here until it is done); returns its ticket."""
+        _need(4, reads_2bit=reads_2bit, lens=lens, out_bwt=out_bwt)
+        _need(8, out_dollar_pos=out_dollar_pos, out_counts=out_counts)
         lens_n = int(lens.numel() if _is_tensor(lens) else np.asarray(lens).size)
         req = Request(_ptr(reads_2bit), lens_n, _ptr(lens), _ptr(out_bwt), _ptr(out_dollar_pos), _ptr(out_counts))
         t = ctypes.c_uint64()
@@ -183,6 +185,8 @@ def build_noalloc(reads_2bit, lens_host, out_bwt, out_dollar_pos, out_counts, st
     """cxbwt_build_noalloc: device reads and outputs (torch CUDA tensors),
     host lengths (numpy uint32).  Allocates nothing; raises CxbwtError on a
     negative status."""
+    _need(4, reads_2bit=reads_2bit, out_bwt=out_bwt)
+    _need(8, out_dollar_pos=out_dollar_pos, out_counts=out_counts)
     lens_host = np.ascontiguousarray(lens_host, dtype=np.uint32)
     st = lib().cxbwt_build_noalloc(_ptr(reads_2bit), lens_host.size, lens_host.ctypes.data, _ptr(out_bwt),
                                    _ptr(out_dollar_pos), _ptr(out_counts), _stream_ptr(stream))
@@ -236,6 +240,20 @@ def _ptr(x):
 
 def _nbytes(x):
     return x.numel() * x.element_size() if _is_tensor(x) else x.nbytes
+
+
+def _need(size: int, **arrays):
+    """Raise TypeError unless every given array or tensor (None: skipped) has
+    elements of `size` bytes: the library reads packed words and lengths as
+    uint32 and writes $ rows, counts and suffix entries as uint64, so an
+    int64 length array, say, would otherwise be read as other lengths."""
+    for name, x in arrays.items():
+        if x is None or not (_is_tensor(x) or isinstance(x, np.ndarray)):
+            continue
+        got = x.element_size() if _is_tensor(x) else x.itemsize
+        if got != size:
+            raise TypeError(f"{name} needs {size}-byte elements ({'uint32' if size == 4 else 'uint64'}), "
+                            f"got {x.dtype}")
 
 
 def _check(status: int, ctx=None):
@@ -394,6 +412,8 @@ class Context:
                     out_counts = np.zeros(5, dtype=np.uint64)
                 if want_sa and out_sa is None:
                     out_sa = np.zeros(total, dtype=np.uint64)
+        _need(4, reads_2bit=reads_2bit, lens=lens, out_bwt=out_bwt)
+        _need(8, out_dollar_pos=out_dollar_pos, out_counts=out_counts, out_sa=out_sa)
         st = _stream_ptr(stream)
         L = lib()
         if want_sa or out_sa is not None:
@@ -408,6 +428,7 @@ class Context:
 
     def bucket_counts(self, reads_2bit, lens, stream=None) -> np.ndarray:
         """Suffixes per 8-base bucket (BUCKETS entries; reads of one length)."""
+        _need(4, reads_2bit=reads_2bit, lens=lens)
         n = int(lens.numel() if _is_tensor(lens) else np.asarray(lens).size)
         out = np.zeros(BUCKETS, dtype=np.uint64)
         _check(lib().cxbwt_bucket_counts(self._h, _ptr(reads_2bit), n, _ptr(lens), out.ctypes.data,
@@ -444,6 +465,8 @@ class Context:
                 out_dollar_pos = np.zeros(n, dtype=np.uint64)
             if out_counts is None:
                 out_counts = np.zeros(5, dtype=np.uint64)
+        _need(4, reads_2bit=reads_2bit, lens=lens, out_words=out_words)
+        _need(8, out_dollar_pos=out_dollar_pos, out_counts=out_counts)
         if _nbytes(out_words) < 4 * part_words(row0, rows):
             raise ValueError("out_words holds fewer words than the part needs")
         r0, nr = ctypes.c_uint64(), ctypes.c_uint64()
@@ -461,6 +484,8 @@ class Context:
         arr = (Collection * len(collections))()
         keep = []
         for i, (words, lens, bwt, dpos, cnt) in enumerate(collections):
+            _need(4, reads_2bit=words, lens=lens, out_bwt=bwt)
+            _need(8, out_dollar_pos=dpos, out_counts=cnt)
             n = int(lens.numel() if _is_tensor(lens) else np.asarray(lens).size)
             arr[i] = Collection(_ptr(words), n, _ptr(lens), _ptr(bwt), _ptr(dpos), _ptr(cnt))
             keep.append((words, lens, bwt, dpos, cnt))
@@ -469,6 +494,8 @@ class Context:
 
     def autotune(self, reads_2bit, lens, scratch_bwt, scratch_dollar_pos=None, stream=None) -> dict:
         """Time the candidate plans on this collection; later builds of its size class use the fastest."""
+        _need(4, reads_2bit=reads_2bit, lens=lens, scratch_bwt=scratch_bwt)
+        _need(8, scratch_dollar_pos=scratch_dollar_pos)
         n = int(lens.numel() if _is_tensor(lens) else np.asarray(lens).size)
         t = Tuning()
         _check(lib().cxbwt_autotune(self._h, _ptr(reads_2bit), n, _ptr(lens), _ptr(scratch_bwt),

@@ -128,3 +128,20 @@ def test_binding_signatures_match_the_header():
         restype, argtypes = binding.SIGNATURES[name]
         assert len(argtypes) == n, name
         assert (restype is not None) == returns, name
+
+
+def test_binding_rejects_wrong_element_sizes():
+    """Arrays whose elements the library would misread are refused before
+    any call: lengths as int64, packed words as uint8 codes, $ rows as
+    uint32."""
+    import torch
+
+    from paper_1401_7457_gb300 import binding
+    binding._need(4, reads_2bit=np.zeros(3, dtype=np.uint32), lens=torch.zeros(2, dtype=torch.int32), none=None)
+    binding._need(8, out_dollar_pos=np.zeros(2, dtype=np.uint64), out_counts=torch.zeros(5, dtype=torch.int64))
+    with pytest.raises(TypeError, match="lens needs 4-byte"):
+        binding._need(4, lens=np.array([100, 100]))  # numpy's default int64
+    with pytest.raises(TypeError, match="reads_2bit needs 4-byte"):
+        binding._need(4, reads_2bit=np.zeros(16, dtype=np.uint8))
+    with pytest.raises(TypeError, match="out_dollar_pos needs 8-byte"):
+        binding._need(8, out_dollar_pos=torch.zeros(2, dtype=torch.int32))
