@@ -75,8 +75,11 @@ typedef struct cxbwt_ctx cxbwt_ctx;
 typedef struct {
   uint64_t device_budget_bytes; /* cap on device memory the context may hold; 0 = 90% of free memory */
   int device;                   /* CUDA device ordinal */
-  int prefix_len;               /* l of the bucket plan (Section 3.1); 0 = automatic */
-  int digit_bits;               /* radix digit width; 8 is the only width built (0 = 8) */
+  int prefix_len;               /* l of the bucket plan (Section 3.1): must be 0, the planner chooses it
+                                   (4- or 8-base buckets for slices and parts, 16 bases for the group plan);
+                                   any other value gives CXBWT_EUNSUPPORTED */
+  int digit_bits;               /* radix digit width; 8 is the only width built (0 = 8, others give
+                                   CXBWT_EUNSUPPORTED) */
   int tile_items;               /* items per radix tile; 0 = automatic */
   int async;                    /* nonzero: calls return after enqueue when outputs are on the device */
   int timing;                   /* nonzero: record CUDA events around every phase (see cxbwt_stats) */

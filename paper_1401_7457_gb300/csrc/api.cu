@@ -791,6 +791,10 @@ int cxbwt_create(cxbwt_ctx** out, const cxbwt_options* opt) {
     g_create_error = "digit_bits: only 8-bit digits are built";
     return CXBWT_EUNSUPPORTED;
   }
+  if (o.prefix_len != 0) {
+    g_create_error = "prefix_len: the planner chooses the bucket prefix itself (leave it 0)";
+    return CXBWT_EUNSUPPORTED;
+  }
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || ndev == 0) {

@@ -145,3 +145,16 @@ def test_binding_rejects_wrong_element_sizes():
         binding._need(4, reads_2bit=np.zeros(16, dtype=np.uint8))
     with pytest.raises(TypeError, match="out_dollar_pos needs 8-byte"):
         binding._need(8, out_dollar_pos=torch.zeros(2, dtype=torch.int32))
+
+
+def test_create_rejects_options_it_does_not_build(lib):
+    """Checked before any device work, so this runs without a GPU."""
+    from paper_1401_7457_gb300 import binding
+    for field, value in (("prefix_len", 4), ("digit_bits", 4)):
+        opt = binding.Options()
+        lib.cxbwt_default_options(ctypes.byref(opt))
+        setattr(opt, field, value)
+        h = ctypes.c_void_p()
+        assert lib.cxbwt_create(ctypes.byref(h), ctypes.byref(opt)) == -5
+        assert not h.value
+        assert field.encode() in lib.cxbwt_last_error(None)
