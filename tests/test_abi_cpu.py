@@ -158,3 +158,20 @@ def test_create_rejects_options_it_does_not_build(lib):
         assert lib.cxbwt_create(ctypes.byref(h), ctypes.byref(opt)) == -5
         assert not h.value
         assert field.encode() in lib.cxbwt_last_error(None)
+
+
+def test_no_cpu_fallback(lib, monkeypatch):
+    """Without a CUDA device a context cannot be created (CXBWT_ECUDA): the
+    library has no CPU path.  Without the built library the binding raises
+    instead of computing anything itself."""
+    import torch
+
+    from paper_1401_7457_gb300 import binding
+    if not torch.cuda.is_available():
+        with pytest.raises(binding.CxbwtError) as e:
+            binding.Context(device=0)
+        assert e.value.status == -3
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding, "LIB_PATH", os.path.join(ROOT, "no_such_dir", "libcxbwt.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        binding.pack_codes(np.zeros(4, dtype=np.uint8))
