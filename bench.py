@@ -197,6 +197,9 @@ class ClockSampler:
             self.source = "nvidia-smi every 200 ms"
         except Exception:
             self.proc = None
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+            self.path = None
 
     def __exit__(self, *exc):
         if self.thread:

@@ -129,7 +129,7 @@ def test_clock_sampler_without_nvml_or_smi(monkeypatch):
     monkeypatch.setenv("PATH", "/nonexistent")
     with bench.ClockSampler(0) as c:
         pass
-    assert c.summary() is None
+    assert c.summary() is None and c.path is None  # no temporary file left behind
 
 
 def test_summarize_clocks():
