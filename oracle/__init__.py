@@ -56,6 +56,13 @@ def _bind(lib):
     lib.cxo_check_sa.restype = ctypes.c_int64
     lib.cxo_check_sa.argtypes = [ctypes.c_char_p, u64p, u32p, ctypes.c_uint64, u64p, u32p,
                                  ctypes.c_uint64, ctypes.c_int]
+    if hasattr(lib, "cxo_sort_range"):
+        lib.cxo_prefix_counts.restype = ctypes.c_int64
+        lib.cxo_prefix_counts.argtypes = [ctypes.c_char_p, u64p, u32p, ctypes.c_uint64, ctypes.c_int, u64p,
+                                          ctypes.c_int]
+        lib.cxo_sort_range.restype = ctypes.c_int64
+        lib.cxo_sort_range.argtypes = [ctypes.c_char_p, u64p, u32p, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64,
+                                       ctypes.c_uint64, ctypes.c_uint64, u64p, u32p, ctypes.c_char_p, ctypes.c_int]
     return lib
 
 
@@ -167,3 +174,52 @@ def check_sa(col: Collection, sa_read: np.ndarray, sa_pos: np.ndarray, threads: 
     return int((lib or _load()).cxo_check_sa(col.seq, _ptr(col.off, ctypes.c_uint64), _ptr(col.lens, ctypes.c_uint32),
                                     col.n, _ptr(sa_read, ctypes.c_uint64), _ptr(sa_pos, ctypes.c_uint32),
                                     sa_read.size, int(threads)))
+
+
+def prefix_counts(col: Collection, p: int, threads: int = 0, lib=None) -> np.ndarray:
+    """Suffixes per bucket of their first p symbols over $ < A < C < G < T
+    (5**p buckets, base 5, first symbol most significant; positions from the
+    $ on read as $): the partition of Section 3.1."""
+    out = np.zeros(5 ** p, dtype=np.uint64)
+    got = (lib or _load()).cxo_prefix_counts(col.seq, _ptr(col.off, ctypes.c_uint64), _ptr(col.lens, ctypes.c_uint32),
+                                             col.n, int(p), _ptr(out, ctypes.c_uint64), int(threads))
+    if got != col.n_suffixes:
+        raise RuntimeError(f"cxo_prefix_counts returned {got}, expected {col.n_suffixes}")
+    return out
+
+
+def sort_range(col: Collection, p: int, lo: int, hi: int, rows: int, threads: int = 1, lib=None):
+    """The sorted suffixes of buckets [lo, hi) (``rows`` of them, from
+    ``prefix_counts``): ``(bwt, sa_read, sa_pos)`` as ``sort`` returns them
+    for those rows of the whole order."""
+    sa_read = np.empty(rows, dtype=np.uint64)
+    sa_pos = np.empty(rows, dtype=np.uint32)
+    out = ctypes.create_string_buffer(max(rows, 1))
+    got = (lib or _load()).cxo_sort_range(col.seq, _ptr(col.off, ctypes.c_uint64), _ptr(col.lens, ctypes.c_uint32),
+                                          col.n, int(p), int(lo), int(hi), int(rows), _ptr(sa_read, ctypes.c_uint64),
+                                          _ptr(sa_pos, ctypes.c_uint32), out, int(threads))
+    if got != rows:
+        raise RuntimeError(f"cxo_sort_range returned {got}, expected {rows}")
+    return out.raw[:rows], sa_read, sa_pos
+
+
+def sorted_ranges(col: Collection, p: int = 4, max_rows: int = 500_000_000, threads: int = 1, lib=None):
+    """The whole sorted suffix list, one range of consecutive prefix buckets at
+    a time (each of at most ``max_rows`` suffixes unless one bucket alone is
+    larger): yields ``(row0, bwt, sa_read, sa_pos)`` with row0 the rank of
+    the range's first suffix.  Concatenated, the ranges are ``sort``'s
+    result."""
+    counts = prefix_counts(col, p, threads, lib)
+    row0 = 0
+    b = 0
+    nb = counts.size
+    while b < nb:
+        e, rows = b, 0
+        while e < nb and (e == b or rows + int(counts[e]) <= max_rows):
+            rows += int(counts[e])
+            e += 1
+        if rows:
+            bwt_r, sr, sp = sort_range(col, p, b, e, rows, threads, lib)
+            yield row0, bwt_r, sr, sp
+        row0 += rows
+        b = e

@@ -33,6 +33,17 @@
 //   cxo_check_sa  - certifies that a given suffix list is every suffix once,
 //                   in strictly increasing order (a proof of sortedness that
 //                   holds at any size).
+//   cxo_prefix_counts, cxo_sort_range
+//                 - the same sort one range of prefix buckets at a time, for
+//                   collections whose whole suffix list does not fit in host
+//                   memory.  Section 3.1 partitions the suffixes by their
+//                   first l symbols: two suffixes whose first l symbols differ
+//                   are ordered by those symbols alone, so sorting every
+//                   bucket on its own and concatenating the buckets in bucket
+//                   order gives the whole order.  Here a bucket is the first p
+//                   symbols over $ < A < C < G < T (every position from the $
+//                   on reads as $), and within a bucket the comparator below
+//                   decides, unchanged.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -69,6 +80,19 @@ inline bool suffix_less(const Reads& R, const Suffix& a, const Suffix& b) {
   return a.read < b.read;
 }
 
+// Writes the sorted list: the suffix of each rank and its BWT symbol, the
+// symbol preceding the suffix in its own read, or $ at position 0 (Section 2).
+inline void write_sorted(const Reads& R, const std::vector<Suffix>& list, uint64_t* out_read, uint32_t* out_pos,
+                         char* out_bwt) {
+  const uint64_t total = list.size();
+  for (uint64_t r = 0; r < total; ++r) {
+    const Suffix& s = list[r];
+    if (out_read) out_read[r] = s.read;
+    if (out_pos) out_pos[r] = s.pos;
+    if (out_bwt) out_bwt[r] = s.pos == 0 ? '$' : R.seq[R.off[s.read] + s.pos - 1];
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -99,13 +123,7 @@ int64_t cxo_sort(const char* seq, const uint64_t* off, const uint32_t* len, uint
   (void)threads;
   std::sort(list.begin(), list.end(), cmp);
 #endif
-  for (uint64_t r = 0; r < total; ++r) {
-    const Suffix& s = list[r];
-    if (out_read) out_read[r] = s.read;
-    if (out_pos) out_pos[r] = s.pos;
-    // Preceding symbol of the suffix in its own read; $ at position 0.
-    if (out_bwt) out_bwt[r] = s.pos == 0 ? '$' : seq[off[s.read] + s.pos - 1];
-  }
+  write_sorted(R, list, out_read, out_pos, out_bwt);
   return int64_t(total);
 }
 
@@ -169,6 +187,117 @@ int64_t cxo_check_sa(const char* seq, const uint64_t* off, const uint32_t* len, 
   }
   (void)threads;
   return first_bad;
+}
+
+// Bucket of suffix (i, k): its first p symbols, each $ = 0, A = 1, C = 2,
+// G = 3, T = 4, as a base-5 number with the first symbol most significant;
+// every position from the $ on is 0 (the suffix has ended there).
+static inline uint64_t prefix_bucket(const char* seq, const uint64_t* off, const uint32_t* len, uint64_t i,
+                                     uint32_t k, int p) {
+  uint64_t code = 0;
+  for (int t = 0; t < p; ++t) {
+    uint64_t s = 0;
+    if (k + uint32_t(t) < len[i]) {
+      switch (seq[off[i] + k + t]) {
+        case 'A': s = 1; break;
+        case 'C': s = 2; break;
+        case 'G': s = 3; break;
+        default: s = 4; break;  // 'T'
+      }
+    }
+    code = code * 5 + s;
+  }
+  return code;
+}
+
+// counts[b] = number of suffixes in bucket b, for b < 5^p (1 <= p <= 12).
+// Returns N, or -1 on a bad argument.
+int64_t cxo_prefix_counts(const char* seq, const uint64_t* off, const uint32_t* len, uint64_t n, int p,
+                          uint64_t* counts, int threads) {
+  if (!seq || !off || !len || !counts || p < 1 || p > 12) return -1;
+  uint64_t buckets = 1;
+  for (int t = 0; t < p; ++t) buckets *= 5;
+  std::memset(counts, 0, buckets * sizeof(uint64_t));
+  uint64_t total = 0;
+#ifdef _OPENMP
+  if (threads > 0) omp_set_num_threads(threads);
+#pragma omp parallel
+#endif
+  {
+    std::vector<uint64_t> mine(buckets, 0);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 4096) nowait
+#endif
+    for (int64_t i = 0; i < int64_t(n); ++i)
+      for (uint32_t k = 0; k <= len[i]; ++k) ++mine[prefix_bucket(seq, off, len, uint64_t(i), k, p)];
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+    for (uint64_t b = 0; b < buckets; ++b) counts[b] += mine[b];
+  }
+  (void)threads;
+  for (uint64_t b = 0; b < buckets; ++b) total += counts[b];
+  return int64_t(total);
+}
+
+// Sorts the suffixes whose bucket (first p symbols, as above) lies in
+// [bucket_lo, bucket_hi) and writes them, smallest first, as cxo_sort does
+// (out_read, out_pos, out_bwt: `capacity` entries each, any may be NULL).
+// Their ranks in the whole order are those of cxo_sort offset by the number
+// of suffixes in the buckets below bucket_lo.  Returns the number written,
+// -1 on a bad argument, or -2 when they are more than `capacity`.
+int64_t cxo_sort_range(const char* seq, const uint64_t* off, const uint32_t* len, uint64_t n, int p,
+                       uint64_t bucket_lo, uint64_t bucket_hi, uint64_t capacity, uint64_t* out_read,
+                       uint32_t* out_pos, char* out_bwt, int threads) {
+  if (!seq || !off || !len || p < 1 || p > 12 || bucket_lo > bucket_hi) return -1;
+  const Reads R{seq, off, len};
+  std::vector<Suffix> list;
+  // List the range's suffixes (in read order; the sort decides the rest).
+  {
+    int nt = 1;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+    nt = threads > 0 ? threads : omp_get_max_threads();
+#endif
+    std::vector<std::vector<Suffix>> parts(static_cast<size_t>(nt));
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nt)
+#endif
+    {
+      int me = 0;
+#ifdef _OPENMP
+      me = omp_get_thread_num();
+#endif
+      std::vector<Suffix>& mine = parts[size_t(me)];
+      const uint64_t lo = n * uint64_t(me) / uint64_t(nt), hi = n * uint64_t(me + 1) / uint64_t(nt);
+      for (uint64_t i = lo; i < hi; ++i)
+        for (uint32_t k = 0; k <= len[i]; ++k) {
+          const uint64_t b = prefix_bucket(seq, off, len, i, k, p);
+          if (b >= bucket_lo && b < bucket_hi) mine.push_back(Suffix{i, k});
+        }
+    }
+    uint64_t total = 0;
+    for (const auto& v : parts) total += v.size();
+    if (total > capacity) return -2;
+    list.reserve(total);
+    for (auto& v : parts) {
+      list.insert(list.end(), v.begin(), v.end());
+      std::vector<Suffix>().swap(v);
+    }
+  }
+  auto cmp = [&R](const Suffix& a, const Suffix& b) { return suffix_less(R, a, b); };
+#ifdef _OPENMP
+  if (threads > 1) {
+    omp_set_num_threads(threads);
+    __gnu_parallel::sort(list.begin(), list.end(), cmp);
+  } else {
+    std::sort(list.begin(), list.end(), cmp);
+  }
+#else
+  std::sort(list.begin(), list.end(), cmp);
+#endif
+  write_sorted(R, list, out_read, out_pos, out_bwt);
+  return int64_t(list.size());
 }
 
 }  // extern "C"

@@ -21,11 +21,16 @@ MUTANTS = {
     "alphabet_reversed": ("if (c != 0) return c < 0;", "if (c != 0) return c > 0;"),
     "last_symbol_not_compared": ("const uint32_t m = la < lb ? la : lb;",
                                  "const uint32_t m = la < lb ? (la ? la - 1 : 0) : (lb ? lb - 1 : 0);"),
-    "preceding_symbol_off_by_one": ("seq[off[s.read] + s.pos - 1]", "seq[off[s.read] + s.pos]"),
-    "dollar_at_wrong_end": ("s.pos == 0 ? '$'", "s.pos == len[s.read] ? '$'"),
+    "preceding_symbol_off_by_one": ("R.seq[R.off[s.read] + s.pos - 1]", "R.seq[R.off[s.read] + s.pos]"),
+    "dollar_at_wrong_end": ("s.pos == 0 ? '$'", "s.pos == R.len[s.read] ? '$'"),
     "rank_counts_equal_suffix": ("if (suffix_less(R, Suffix{uint64_t(i), k}, q)) ++count;",
                                  "if (!suffix_less(R, q, Suffix{uint64_t(i), k})) ++count;"),
     "certificate_skips_last_pair": ("for (int64_t r = 0; r < last; ++r) {", "for (int64_t r = 0; r < last - 1; ++r) {"),
+    "bucket_symbol_order_reversed": ("code = code * 5 + s;", "code = code * 5 + (4 - s);"),
+    "bucket_end_marker_above_bases": ("    uint64_t s = 0;\n    if (k + uint32_t(t) < len[i]) {",
+                                      "    uint64_t s = 5;\n    if (k + uint32_t(t) < len[i]) {"),
+    "range_drops_its_first_bucket": ("if (b >= bucket_lo && b < bucket_hi) mine.push_back",
+                                     "if (b > bucket_lo && b < bucket_hi) mine.push_back"),
 }
 
 RUNNER = r"""

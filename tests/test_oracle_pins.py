@@ -142,3 +142,36 @@ def test_oracle_reproduces_its_stored_digest():
     assert pins.result_digest(bytes(flipped), res["dollar_pos"], res["counts"]) != want["sha256"]
     assert pins.result_digest(res["bwt"], res["dollar_pos"] + np.uint64(1), res["counts"]) != want["sha256"]
     assert pins.result_digest(res["bwt"], res["dollar_pos"], res["counts"][::-1]) != want["sha256"]
+
+
+def test_prefix_ranges_match_brute_force():
+    """The oracle's sort one range of prefix buckets at a time (Section 3.1:
+    suffixes whose first l symbols differ are ordered by those symbols, so the
+    buckets sort independently and concatenate in bucket order) against the
+    brute-force rotation order, for bucket prefixes of 1 to 4 symbols and
+    ranges down to one bucket each; reads shorter than the prefix end inside
+    it."""
+    rng = np.random.default_rng(31)
+    for _ in range(400):
+        k = int(rng.integers(1, 7))
+        alpha = "ACGT"[: int(rng.integers(1, 5))]
+        reads = ["".join(rng.choice(list(alpha), size=int(rng.integers(1, 9)))) for _ in range(k)]
+        p = int(rng.integers(1, 5))
+        assert pins.prefix_ranges_match(reads, p, int(rng.integers(1, 12))), (reads, p)
+
+
+def test_prefix_ranges_equal_the_whole_sort():
+    """At a moderate size (genome-like reads, long shared prefixes), the
+    ranges concatenate to exactly the whole sort, and the bucket counts sum
+    to N."""
+    g = synth.random_genome(20_000, 41)
+    codes, lens = synth.sample_reads(g, 3000, 100, 42, 0.01)
+    col = oracle.Collection(codes, lens)
+    ref = oracle.bwt(col, threads=2)
+    counts = oracle.prefix_counts(col, 3, threads=2)
+    assert int(counts.sum()) == col.n_suffixes and counts[0] == col.n  # bucket "$$$": the terminator-only suffixes
+    parts = list(oracle.sorted_ranges(col, 3, 20_000, threads=2))
+    assert len(parts) > 5
+    assert b"".join(b for _, b, _, _ in parts) == ref["bwt"]
+    assert np.array_equal(np.concatenate([r for _, _, r, _ in parts]), ref["sa_read"])
+    assert np.array_equal(np.concatenate([q for _, _, _, q in parts]), ref["sa_pos"])
