@@ -127,7 +127,7 @@ int build_pack(cxbwt_ctx* c, const cxbwt_collection* colls, const std::vector<ui
   CX_TRY(ensure(c, c->P, uint64_t(L) * kRadix * 4, "position counts"));
   CX_TRY(ensure(c, c->base, uint64_t(pl.D + 6) * kRadix * 4, "digit bases"));
   CX_TRY(ensure(c, c->lenhist, 4, "length histogram"));
-  CX_TRY(ensure(c, c->seglist, (pl.N / 33 + 1 + pl.N / kCtaMax + 1) * 8, "group lists"));
+  CX_TRY(ensure(c, c->seglist, (cta_list_cap(pl.N) + big_list_cap(pl.N, pl.seg_words)) * 8, "group lists"));
   CX_TRY(ensure(c, c->rhist, size_t(pl.W) * 4 * kRadix * 4, "group digit counts"));
   // Per-collection counts (5 each) after the pack's own counters.
   CX_TRY(ensure(c, c->out_dollar, uint64_t(k) * 5 * 8, "pack counts"));

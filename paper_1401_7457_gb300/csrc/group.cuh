@@ -10,10 +10,16 @@ constexpr uint32_t kCtaMax = 2048;  // largest group remainder finished by one C
 constexpr uint32_t kSmallCta = 256; // remainders up to this size go to small CTAs (128 threads, many per SM)
 // The CTA finish holds (id, key words, index) per row in shared memory: wide
 // keys (long reads) get fewer rows.
+constexpr uint32_t cta_rows_for(int nw) { return nw <= 16 ? kCtaMax : kCtaMax / 2; }
 template <int NW>
 struct CtaRows {
-  static constexpr uint32_t value = NW <= 16 ? kCtaMax : kCtaMax / 2;
+  static constexpr uint32_t value = cta_rows_for(NW);
 };
+// Entries the two group lists need for `rows` rows finished with key width
+// nw: every listed CTA remainder holds more than 32 rows, every big one more
+// than cta_rows_for(nw).
+constexpr uint64_t cta_list_cap(uint64_t rows) { return rows / 33 + 1; }
+constexpr uint64_t big_list_cap(uint64_t rows, int nw) { return rows / (uint64_t(cta_rows_for(nw)) + 1) + 1; }
 
 struct SegArgs {
   const uint32_t* keys;   // first 16-base window of each row, ascending

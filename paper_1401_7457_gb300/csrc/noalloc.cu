@@ -36,7 +36,7 @@ namespace {
 
 constexpr uint64_t kMaxRows = CXBWT_NOALLOC_MAX_SUFFIXES;
 constexpr uint32_t kMaxLen = CXBWT_NOALLOC_MAX_READ_LEN;
-constexpr uint32_t kTile = 4096;                       // onesweep_shape(0, 4)
+constexpr uint32_t kTile = 4096;                       // onesweep_shape(0, 4).tile(), checked at each call
 constexpr uint64_t kMaxTiles = (kMaxRows + kTile - 1) / kTile;
 constexpr uint32_t kMaxD = (kMaxLen + 3) / 4;
 constexpr uint32_t kMaxW = (kMaxLen + 15) / 16;
@@ -51,11 +51,17 @@ constexpr uint64_t kOffKeys1 = align256(kOffKeys0 + kMaxRows * 4);
 constexpr uint64_t kOffStatus = align256(kOffKeys1 + kMaxRows * 4);
 constexpr uint64_t kOffP = align256(kOffStatus + kMaxTiles * kRadix * 8);
 constexpr uint64_t kOffBase = align256(kOffP + uint64_t(kMaxLen) * kRadix * 4);
-constexpr uint64_t kCtaCap = kMaxRows / 33 + 1, kBigCap = kMaxRows / kCtaMax + 1;
+// Reads of at most kMaxLen bases finish their groups with keys of at most
+// 16 words (segsort_words), which sets the CTA size of the group finish.
+static_assert((kMaxLen - 16 + 15) / 16 <= 16, "the group lists below assume keys of at most 16 words");
+constexpr uint64_t kCtaCap = cta_list_cap(kMaxRows), kBigCap = big_list_cap(kMaxRows, 16);
+// Look-back epochs one call may use: the four window-0 passes, then at most
+// 4 per window for every big group.
+constexpr uint32_t kEpochsPerCall = uint32_t(4 + 4 * kMaxW * kBigCap);
 constexpr uint64_t kOffSeg = align256(kOffBase + uint64_t(kMaxD + 5) * kRadix * 4);
 constexpr uint64_t kOffRhist = align256(kOffSeg + (kCtaCap + kBigCap) * 8);
 constexpr uint64_t kOffMisc = align256(kOffRhist + uint64_t(kMaxW) * 4 * kRadix * 4);
-// misc: [0] tile counter, [4] error word, [64] 5 x u64 counts, [128] 4 x u32 group-finish counters
+// misc: [0] tile counter, [4] error word, [64] 5 x u64 counts, [128] 5 x u32 group-finish counters
 constexpr uint64_t kNoallocScratchBytes = align256(kOffMisc + 256);
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
@@ -117,13 +123,16 @@ extern "C" int cxbwt_build_noalloc(const uint32_t* reads_2bit, uint64_t n_reads,
       g_scratch[dev] = p;
     }
     base = static_cast<char*>(g_scratch[dev]);
-    // Look-back flags are 2*epoch and 2*epoch+1 in 32 bits; one call uses at
-    // most 4 + 4 * kMaxW * kBigCap epochs, far below the margin kept here.
-    if (g_epoch[dev] >= (1u << 29)) {
+    // Look-back flags are 2*epoch and 2*epoch+1 in 32 bits.  The call takes
+    // its whole range of epochs now, whatever happens later: a call that
+    // fails half-way leaves flags of its own epochs in the status words, and
+    // no later call uses those epochs again.
+    if (g_epoch[dev] >= (1u << 29) - kEpochsPerCall) {
       NA_CUDA(cudaMemsetAsync(base + kOffStatus, 0, kMaxTiles * kRadix * 8, st));
       g_epoch[dev] = 0;
     }
     epoch = g_epoch[dev];
+    g_epoch[dev] += kEpochsPerCall;
   }
   char* misc = base + kOffMisc;
   auto* d_counter = reinterpret_cast<uint32_t*>(misc);
@@ -150,6 +159,7 @@ extern "C" int cxbwt_build_noalloc(const uint32_t* reads_2bit, uint64_t n_reads,
   void* vals[2] = {base + kOffVals0, base + kOffVals1};
   uint32_t* keys[2] = {reinterpret_cast<uint32_t*>(base + kOffKeys0), reinterpret_cast<uint32_t*>(base + kOffKeys1)};
   const TileShape shape = onesweep_shape(0, 4);
+  if (uint32_t(shape.tile()) != kTile) return CXBWT_EINTERNAL;  // the array was sized for kTile-item tiles
   PassArgs a{};
   a.status = reinterpret_cast<unsigned long long*>(base + kOffStatus);
   a.tile_counter = d_counter;
@@ -251,10 +261,6 @@ extern "C" int cxbwt_build_noalloc(const uint32_t* reads_2bit, uint64_t n_reads,
   e.read_base = 0;
   e.n_reads_out = uint32_t(n_reads);
   NA_CUDA(launch_emit(e, st));
-  {
-    std::lock_guard<std::mutex> lock(g_mu);
-    g_epoch[dev] = epoch;  // the next call's flags never match this call's
-  }
   NA_CUDA(cudaMemcpyAsync(out_counts, d_counts, 40, cudaMemcpyDefault, st));
   uint32_t derr = 0;
   NA_CUDA(cudaMemcpyAsync(&derr, d_err, 4, cudaMemcpyDeviceToHost, st));

@@ -281,3 +281,20 @@ def test_carried_base_batch():
         ref = oracle_of(codes, lens)
         assert binding.unpack_ascii(bwt, dpos, len(ref["bwt"])) == ref["bwt"]
         assert np.array_equal(dpos, ref["dollar_pos"]) and np.array_equal(cnt, ref["counts"])
+
+
+def test_wide_key_groups_larger_than_a_cta():
+    """1,500 identical 300-base reads on the group plan: keys of 24 words, so
+    one CTA finishes at most 1,024 rows, and about 280 groups of 1,500 equal
+    suffixes go to the big-group list (sized from that CTA limit) and are
+    finished by LSD passes over their rows; the result is the oracle's."""
+    from paper_1401_7457_gb300 import binding
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    one = np.random.default_rng(18).integers(0, 4, size=300).astype(np.uint8)
+    codes, lens = np.tile(one, 1500), np.full(1500, 300, dtype=np.uint32)
+    ref = oracle_of(codes, lens)
+    with binding.Context(device=0, algorithm=2) as c:
+        got = gpu_bwt(c, codes, lens, want_sa=True)
+        assert c.stats()["big_groups"] > 221  # more than rows / 2048 + 1 big groups
+    assert_same(got, ref, sa=True)

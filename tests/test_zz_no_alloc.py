@@ -87,3 +87,30 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
     with pytest.raises(binding.CxbwtError) as e:
         binding.build_noalloc(words, mixed, out, dpos, cnt)
     assert e.value.status == -5
+
+
+def test_noalloc_big_groups_on_consecutive_calls():
+    """Groups of more than 2,048 suffixes that share their first 16 bases go
+    to the allocation-free build's own fallback (per-group digit counts and
+    LSD passes over the group's rows, in the static array): 3,000 identical
+    60-base reads and 2,500 all-A reads of 50 bases, each built twice, one
+    after the other, so that each call starts from the other's leftovers.
+    Every result is the oracle's and the same as cxbwt_build's."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    from paper_1401_7457_gb300 import binding
+    one = np.random.default_rng(75).integers(0, 4, size=60).astype(np.uint8)
+    cases = [(np.tile(one, 3000), np.full(3000, 60, dtype=np.uint32)),
+             (np.zeros(2500 * 50, dtype=np.uint8), np.full(2500, 50, dtype=np.uint32))]
+    refs = [oracle.bwt(oracle.Collection(c, l), threads=8) for c, l in cases]
+    with binding.Context(device=0) as ctx:
+        for rep in range(2):
+            for (codes, lens), ref in zip(cases, refs):
+                (rb, rd, rc), (b, d, c) = _both(ctx, codes, lens)
+                assert torch.equal(rb, b) and torch.equal(rd, d) and torch.equal(rc, c), rep
+                N = int(lens.sum()) + lens.size
+                dpos = d.cpu().numpy().view(np.uint64)
+                assert binding.unpack_ascii(b.cpu().numpy().view(np.uint32), dpos, N) == ref["bwt"], rep
+                assert np.array_equal(dpos, ref["dollar_pos"])
+                assert np.array_equal(c.cpu().numpy().view(np.uint64), ref["counts"])
