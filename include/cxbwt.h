@@ -56,7 +56,7 @@
 extern "C" {
 #endif
 
-#define CXBWT_ABI_VERSION 1
+#define CXBWT_ABI_VERSION 2
 
 typedef enum {
   CXBWT_OK = 0,
@@ -139,6 +139,10 @@ typedef struct {
   uint64_t slices;              /* device-memory-bounded slices sorted (one per build when it fits) */
   uint64_t cta_groups;          /* groups of equal first 16 bases finished by one CTA (33 .. 2048 rows) */
   uint64_t big_groups;          /* larger groups, finished with more digit passes */
+  uint64_t carried_pass_launches; /* digit passes (among sort_pass_launches) that load the key window the
+                                     previous pass carried, instead of generating ids or gathering it */
+  uint64_t carried_pass_items;  /* sum over those passes of the items each one moved */
+  double carried_pass_ms;       /* their device time, each pass between its own events (only with `timing`) */
   uint64_t reserved[2];
 } cxbwt_stats;
 
@@ -385,7 +389,9 @@ int cxbwt_reset_stats(cxbwt_ctx* ctx);
  * device work overlaps - from two host threads, or on two streams without
  * synchronisation between them - race on it: callers must serialise them.
  * The first call on a device does that device's set-up (it looks up the
- * array's device address and clears it); make it before any stream capture. */
+ * array's device address and clears it); make it before any stream capture.
+ * Every call waits for its stream: it reads small results (the group-finish
+ * counts, the error word) back to the host before it returns. */
 #define CXBWT_NOALLOC_MAX_SUFFIXES (1u << 21)
 #define CXBWT_NOALLOC_MAX_READ_LEN 272
 int cxbwt_build_noalloc(const uint32_t* reads_2bit, uint64_t n_reads, const uint32_t* lens_host, uint32_t* out_bwt,

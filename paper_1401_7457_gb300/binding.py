@@ -45,7 +45,8 @@ class Stats(ctypes.Structure):
                 ("build_ms", ctypes.c_double), ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
                 ("device_bytes_held", ctypes.c_uint64), ("group_ms", ctypes.c_double), ("emit_ms", ctypes.c_double),
                 ("slices", ctypes.c_uint64), ("cta_groups", ctypes.c_uint64), ("big_groups", ctypes.c_uint64),
-                ("reserved", ctypes.c_uint64 * 2)]
+                ("carried_pass_launches", ctypes.c_uint64), ("carried_pass_items", ctypes.c_uint64),
+                ("carried_pass_ms", ctypes.c_double), ("reserved", ctypes.c_uint64 * 2)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

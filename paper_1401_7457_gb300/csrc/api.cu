@@ -116,7 +116,9 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
     a.key_shift = 0;
     a.window_c0 = 0;
     a.epoch = ++c->epoch;
+    if (tev) CX_TRY(pass_event_begin(c, r));
     CX_CUDA(c, launch_onesweep(a, kSrcInitReadMajor, true, !sl.whole, idb, r.shape, st));
+    if (tev) CX_TRY(pass_event_end(c, r, false));
     cur ^= 1;
     ++r.sort_launches;
     r.sort_items += sl.rows;
@@ -145,8 +147,14 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
       a.window_c0 = uint32_t(16 * w);
       a.epoch = ++c->epoch;
       a.stall_tile0 = (c->opt.plan_flags & CXBWT_PLAN_TEST_STALL) && r.sort_launches == 0 ? 1u : 0u;
+      if (tev) CX_TRY(pass_event_begin(c, r));
       CX_CUDA(c, launch_onesweep(a, mode, write_key, generated && !sl.whole, idb, r.shape, st));
+      if (tev) CX_TRY(pass_event_end(c, r, mode == kSrcCarried));
       a.stall_tile0 = 0;
+      if (mode == kSrcCarried) {
+        ++r.carried_launches;
+        r.carried_items += sl.rows;
+      }
       cur ^= 1;
       if (write_key) kin = kout;
       first = false;
@@ -158,7 +166,7 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
 
   // ---- group plan: finish every group of equal first windows on chip ---------
   if (pl.groups && pl.Lmax > 16) {
-    const uint64_t cta_cap = uint64_t(sl.rows) / 33 + 1, big_cap = uint64_t(sl.rows) / kCtaMax + 1;
+    const uint64_t cta_cap = cta_list_cap(sl.rows), big_cap = big_list_cap(sl.rows, pl.seg_words);
     CX_CUDA(c, cudaMemsetAsync(r.d_seg, 0, 32, st));
     SegArgs g{};
     g.keys = r.keys[kin];
@@ -571,7 +579,7 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   CX_TRY(ensure(c, c->base, uint64_t(std::max<uint32_t>(pl.D + pl.len_passes, 5)) * kRadix * 4, "digit bases"));
   if (pl.uniform && !c->lenhist.p) CX_TRY(ensure(c, c->lenhist, 4, "length histogram"));
   if (pl.groups && pl.Lmax > 16) {
-    CX_TRY(ensure(c, c->seglist, (uint64_t(max_rows) / 33 + 1 + uint64_t(max_rows) / kCtaMax + 1) * 8, "group lists"));
+    CX_TRY(ensure(c, c->seglist, (cta_list_cap(max_rows) + big_list_cap(max_rows, pl.seg_words)) * 8, "group lists"));
     CX_TRY(ensure(c, c->rhist, size_t(pl.W) * 4 * kRadix * 4, "group digit counts"));
   }
   r.d_sa = out_sa;
@@ -675,6 +683,8 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   c->stats.d2h_bytes += r.d2h;
   c->stats.device_bytes_held = c->held;
   c->stats.slices += slices.size();
+  c->stats.carried_pass_launches += r.carried_launches;
+  c->stats.carried_pass_items += r.carried_items;
 
   const bool host_out = !bwt_dev || (out_dollar && !dollar_dev) || (out_counts && !counts_dev) || (out_sa && !sa_dev);
   if (c->opt.async && !host_out) {
@@ -698,6 +708,12 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
       c->stats.sort_pass_ms += ms_sort;
       c->stats.group_ms += ms_group;
       c->stats.emit_ms += ms_emit;
+    }
+    for (uint32_t j = 0; j < r.n_pev; ++j) {
+      if (!r.pev_carried[j]) continue;
+      float ms = 0;
+      CX_CUDA(c, cudaEventElapsedTime(&ms, c->pev[2 * size_t(j)], c->pev[2 * size_t(j) + 1]));
+      c->stats.carried_pass_ms += ms;
     }
     c->stats.build_ms += ms_all;
   }
@@ -848,6 +864,7 @@ void cxbwt_destroy(cxbwt_ctx* c) {
   for (auto& ev : c->slice_done)
     if (ev) cudaEventDestroy(ev);
   for (auto& ev : c->tev) cudaEventDestroy(ev);
+  for (auto& ev : c->pev) cudaEventDestroy(ev);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->h_small) cudaFreeHost(c->h_small);
   delete c;

@@ -43,6 +43,7 @@ struct cxbwt_ctx {
   cudaStream_t side = nullptr;            // device -> host streaming of finished slices
   cudaEvent_t slice_done[2] = {nullptr, nullptr};
   std::vector<cudaEvent_t> tev;           // timing events, 4 per slice (timing option)
+  std::vector<cudaEvent_t> pev;           // timing events, 2 per digit pass of a build (timing option)
   unsigned long long* h_small = nullptr;  // pinned: device error word, length stats
   cudaStream_t last_stream = nullptr;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -230,7 +231,31 @@ struct Run {
   bool read_major = false;        // multi-slice first pass in read-major order
   uint32_t bucket_bits = kBucketBits;  // slices are ranges of buckets of the first bucket_bits / 2 bases
   uint64_t launches = 0, sort_launches = 0, sort_items = 0, d2h = 0;
+  uint64_t carried_launches = 0, carried_items = 0;
+  // Per-pass timing (timing option): pass j ran between events pev[2j] and
+  // pev[2j+1]; pev_carried[j] says whether it was a carried-key pass.
+  uint32_t n_pev = 0;
+  std::vector<uint8_t> pev_carried;
 };
+
+// Records the start event of one timed digit pass (grows the context's pool).
+inline int pass_event_begin(cxbwt_ctx* c, Run& r) {
+  while (c->pev.size() < 2 * size_t(r.n_pev + 1)) {
+    cudaEvent_t ev;
+    CX_CUDA(c, cudaEventCreate(&ev));
+    c->pev.push_back(ev);
+  }
+  CX_CUDA(c, cudaEventRecord(c->pev[2 * size_t(r.n_pev)], r.st));
+  return CXBWT_OK;
+}
+
+// Records the end event of the pass begun last.
+inline int pass_event_end(cxbwt_ctx* c, Run& r, bool carried) {
+  CX_CUDA(c, cudaEventRecord(c->pev[2 * size_t(r.n_pev) + 1], r.st));
+  r.pev_carried.push_back(carried ? 1 : 0);
+  ++r.n_pev;
+  return CXBWT_OK;
+}
 
 // Reads the device error word (already copied to h_small[4] by a completed
 // call), clears it, and turns it into a status.  The word is sticky on the
