@@ -1,19 +1,26 @@
 """Benchmark: BWT build throughput (Gbase/s) of one read collection per GPU.
 
-Workload (N=1 default): 1M reads x 100 bp sampled from both strands of a
-seeded 5 Mbp random genome (20x coverage) with 1% substitutions, 101M
-suffixes.  One step = one whole ``cxbwt_build`` (histogram, every radix pass,
-emission) on device-resident input.  ``value`` = bases of all ranks / max over
-ranks of the summed device time of K steps (CUDA events on the build stream;
-L2 flushed by a 512 MB write between steps, outside the timed events).
+Workload (N=1 default): the repeat-rich collection, 50M reads x 100 bp
+sampled from both strands of a seeded 100 Mbp random genome in which 5% of
+the sequence is 10-copy 1 kb repeats at 0.5% divergence, with 1%
+substitutions (50x coverage): 5.05G suffixes, more than one 32-bit-row
+slice, so the build runs in device-memory-bounded bucket slices (Figure 2
+of the paper) with 64-bit suffix ids.  One step = one whole ``cxbwt_build``
+(histograms, every radix pass of every slice, group finish, emission) on
+device-resident input.  ``value`` = bases of all ranks / max over ranks of
+the summed device time of K steps (CUDA events on the build stream; L2
+flushed by a 512 MB write between steps, outside the timed events; the
+working set, about 100 GB, is far larger than L2 anyway).
 
 Extra keys: ``e2e`` (same metric through the C ABI with pinned host buffers,
-copies inside the timed region), ``roofline`` of the dominant kernel (the
-onesweep digit pass, 16 algorithmic bytes per suffix per pass, timed live
-with the library's own CUDA events), ``phases`` (every phase of a build
-against its own algorithmic bytes), ``cpu_baseline`` (the oracle on a bounded
-sample on this host's cores, rank 0 only), ``clocks`` (nvidia-smi sampled
-during the timed region) and ``gpu_launches``.
+input copy and the streamed BWT, $ rows and counts inside the timed region),
+``roofline`` of the dominant kernel (the onesweep carried-key digit pass:
+key and id read and written, 24 B per item with 64-bit ids, each pass timed
+live between the library's own CUDA events), ``phases`` (every phase of a
+build against its own algorithmic bytes), ``cpu_baseline`` (the oracle on a
+bounded sample on this host's cores, rank 0 only), ``clocks`` (sampled during
+the timed region), ``gpu_launches`` and ``config2`` (the same measurement on
+the genome-like collection: 1M reads x 100 bp from a 5 Mbp genome at 20x).
 
 ``--impl reference`` times the CPU oracle instead (the reference arm of this
 method is the definition itself): each step sorts a bounded sample of the same
@@ -41,12 +48,19 @@ METRIC = "BWT build Gbases/s at 1 GB300 (% HBM roofline); served p50/p99 vs plai
 UNIT = "Gbase/s"
 WORKLOAD = ("genome-like: {n:,} reads x 100 bp from both strands of a seeded 5 Mbp uniform genome "
             "(1M reads = 20x coverage), 1% substitutions, seed 2; {N:,} suffixes")
+WORKLOAD_READS = {"genome-like": 1_000_000, "repeat-rich": 50_000_000, "tiny": 10_000}
 WORKLOADS = {
     "genome-like": WORKLOAD,
     "repeat-rich": ("repeat-rich: {n:,} reads x 100 bp from a seeded 100 Mbp genome, 5% in 10-copy 1 kb repeats "
                     "at 0.5% divergence, both strands, 1% substitutions, seed 3; {N:,} suffixes"),
     "tiny": "tiny: {n:,} reads x 100 bp, i.i.d. uniform bases, seed 1; {N:,} suffixes",
 }
+
+
+# Reads are drawn in chunks of this many (synth.sample_reads): a draw of a
+# multiple of it starts with exactly the reads of any larger draw, so the CPU
+# samples below are the workload's own first reads without drawing it whole.
+SAMPLE_CHUNK = 1 << 17
 
 
 def load_workload(name, rank=0, n_reads=0):
@@ -64,7 +78,9 @@ def load_workload(name, rank=0, n_reads=0):
     return WORKLOADS[name], codes, lens
 
 
-PROFILE = os.path.join(ROOT, "profiles", "onesweep_digit_pass_genome_like.md")
+# ncu summaries of the carried-key digit pass, by suffix id width.
+PROFILES = {4: os.path.join(ROOT, "profiles", "onesweep_digit_pass_genome_like.md"),
+            8: os.path.join(ROOT, "profiles", "onesweep_carried_pass_repeat_rich.md")}
 KERNEL_SRC = os.path.join(ROOT, "paper_1401_7457_gb300", "csrc", "onesweep.cuh")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -96,11 +112,12 @@ def id_bytes(n_reads: int, read_len: int, store_bytes: int) -> int:
     return 4 if (n_reads - 1) < (1 << (32 - len_bits)) else 8
 
 
-def profiled_traffic():
-    """DRAM bytes per item of the digit pass from the committed ncu summary,
-    or None when that summary is missing or the kernel changed since."""
+def profiled_traffic(idb):
+    """DRAM bytes per item of the carried-key digit pass with idb-byte ids
+    from the committed ncu summary, or None when that summary is missing or
+    the kernel source changed since it was taken."""
     try:
-        text = open(PROFILE).read()
+        text = open(PROFILES[idb]).read()
     except OSError:
         return None
     m = re.search(r"dram_bytes_per_item:\s*([0-9.]+)", text)
@@ -279,7 +296,16 @@ def phase_rates(st, steps, n_reads, bases, idb, peak):
     group_ms = st["group_ms"] / steps
     emit_ms = st["emit_ms"] / steps
     rest_ms = st["build_ms"] / steps - sort_ms - group_ms - emit_ms
+    carried_ms = st["carried_pass_ms"] / steps
+    gen_items = (st["sort_pass_items"] - st["carried_pass_items"]) / steps
+    slices = st["slices"] / steps
     model = {"digit_passes": (sort_ms, (8 + 2 * idb) * st["sort_pass_items"] / steps),
+             # carried-key passes: key and id read and written
+             "carried_passes": (carried_ms, (8 + 2 * idb) * st["carried_pass_items"] / steps),
+             # passes that make the ids (generated in the first pass of each
+             # slice) or gather a key window: key and id written, the store
+             # read once per slice
+             "generating_passes": (sort_ms - carried_ms, (4 + idb) * gen_items + slices * bases / 4),
              "group_finish": (group_ms, (4 + 2 * idb) * N),
              "emission": (emit_ms, idb * N + N / 4 + 8 * n_reads + bases / 4),
              "histograms_and_planning": (rest_ms, bases / 4 + 4 * n_reads)}
@@ -315,9 +341,8 @@ def cpu_model():
 def cpu_oracle_rate(codes, lens, n_sample_reads, threads):
     """Oracle throughput on the first n_sample_reads reads: (Gbase/s, seconds, bases)."""
     import oracle
-    L = int(lens[0])
     n_s = min(n_sample_reads, lens.size)
-    sc, sl = codes[:n_s * L], lens[:n_s]
+    sc, sl = codes[:int(lens[:n_s].sum())], lens[:n_s]
     col = oracle.Collection(sc, sl)
     t0 = time.perf_counter()
     oracle.sort(col, threads=threads)
@@ -332,9 +357,13 @@ def run_reference(args, rank, world):
         return 0
     import oracle
     oracle.build()
-    desc, codes, lens = load_workload(args.workload, 0, args.reads)
-    threads = os.cpu_count() or 1
     n_sample = args.cpu_sample_reads
+    # Only the sample's reads are drawn (a whole number of draw chunks: the
+    # workload's own first reads); the description names the whole workload.
+    n_full = args.reads or WORKLOAD_READS[args.workload]
+    desc = WORKLOADS[args.workload]
+    _, codes, lens = load_workload(args.workload, 0, min(n_full, -(-n_sample // SAMPLE_CHUNK) * SAMPLE_CHUNK))
+    threads = os.cpu_count() or 1
     for _ in range(args.warmup):
         cpu_oracle_rate(codes, lens, n_sample // 4, threads)
     times = []
@@ -345,10 +374,11 @@ def run_reference(args, rank, world):
     total = sum(times)
     value = bases * args.steps / total / 1e9
     sample = f"first {n_sample:,} reads ({bases:,} bases) of the workload per step, std::sort / parallel-mode sort"
+    L = int(lens[0])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-            "data": "synthetic", "config": {"workload": desc.format(n=lens.size, N=int(lens.sum()) + lens.size)},
+            "data": "synthetic", "config": {"workload": desc.format(n=n_full, N=n_full * (L + 1))},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "cpu_model": cpu_model(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -418,15 +448,46 @@ def run_batch_bench(args, rank, world):
     return 0
 
 
+def oracle_item_digests(name):
+    """Packed digests of the oracle's results for the items of the batched or
+    served workload (tests/golden/oracle_digests.json, written by a script
+    that calls only the oracle), or None when they are not stored."""
+    p = os.path.join(ROOT, "tests", "golden", "oracle_digests.json")
+    try:
+        with open(p) as f:
+            return [it["packed_sha256"] for it in json.load(f)[name]["items"]]
+    except (OSError, KeyError):
+        return None
+
+
+def packed_digest(words, dpos, cnt):
+    """SHA-256 of one result in packed form (the BWT words, then the $ rows
+    and the counts as little-endian integers), the form the stored oracle
+    digests take."""
+    h = hashlib.sha256()
+    h.update(memoryview(np.ascontiguousarray(words, dtype="<u4")).cast("B"))
+    h.update(np.ascontiguousarray(dpos, dtype="<u8").tobytes())
+    h.update(np.ascontiguousarray(cnt, dtype="<u8").tobytes())
+    return h.hexdigest()
+
+
 def run_serve_bench(args, rank, world):
-    """The served workload: 256 requests (n log-uniform in [50k, 5M], length 100
-    or 150, i.i.d. reads with per-request seeds) arriving as an open-loop
-    Poisson stream at 0.8x the plain loop's measured capacity.  The plain loop
-    builds one request at a time with cxbwt_build (pinned host buffers); its
-    latencies follow from its measured build times as a single FIFO server.
-    The served run submits each request at its arrival time to a cxbwt server
-    (continuous batching, 3 workers).  Prints one JSON line with p50/p99
-    latency and aggregate Gbase/s of both (not the benchmark's default line)."""
+    """The served workload: 256 requests (n log-uniform in [50k, 5M], length
+    100 or 150, i.i.d. reads with per-request seeds) arriving as open-loop
+    Poisson streams at 0.5, 0.8, 1.0 and 1.5 times the plain loop's measured
+    capacity (one seeded arrival trace per load).  Under each trace, in real
+    time:
+
+    * the plain loop: one cxbwt_build at a time, first come first served,
+      pinned host buffers;
+    * the server: cxbwt_submit at each arrival time (continuous batching,
+      3 workers).
+
+    Latency = completion - arrival.  Every result of every run is compared
+    with the oracle's stored digest of that request.  One JSON line with
+    p50/p99 latency and aggregate Gbase/s of both per load (not the
+    benchmark's default line)."""
+    import collections
     import threading
 
     import torch
@@ -435,6 +496,7 @@ def run_serve_bench(args, rank, world):
     build.build()
     k = args.reads or 256
     reqs = synth.serve_requests(k=k)
+    want = oracle_item_digests("served")
     inputs = []
     total_bases = 0
     for rq in reqs:
@@ -444,82 +506,107 @@ def run_serve_bench(args, rank, world):
         N = int(lens.sum()) + lens.size
         inputs.append((words, lt, N, lens.size))
         total_bases += int(lens.sum())
+    outs = [(torch.empty((N + 15) // 16, dtype=torch.int32).pin_memory(), torch.empty(n, dtype=torch.int64).pin_memory(),
+             torch.zeros(5, dtype=torch.int64).pin_memory()) for (_, _, N, n) in inputs]
 
-    def outputs(N, n):
-        return (torch.empty((N + 15) // 16, dtype=torch.int32).pin_memory(), torch.empty(n, dtype=torch.int64).pin_memory(),
-                torch.zeros(5, dtype=torch.int64).pin_memory())
+    def check_and_clear():
+        """Digests of every result against the oracle's (when stored); then zero the outputs."""
+        ok = None
+        if want is not None:
+            ok = all(packed_digest(o[0].numpy().view(np.uint32), o[1].numpy(), o[2].numpy()) == d
+                     for o, d in zip(outs, want[:len(outs)]))
+        for o in outs:
+            for t in o:
+                t.zero_()
+        return ok
 
-    # Plain loop: every request alone, back to back (service times).
-    ctx = binding.Context(device=0, budget_bytes=int(args.budget_gb * (1 << 30)))
-    warm = outputs(inputs[0][2], inputs[0][3])
-    ctx.build(inputs[0][0], inputs[0][1], *warm)
+    budget = int(args.budget_gb * (1 << 30))
+    ctx = binding.Context(device=0, budget_bytes=budget)
+    ctx.build(inputs[0][0], inputs[0][1], *outs[0])  # warm-up
+    # Service times of the plain loop (every request alone, back to back).
     service = []
-    outs = [outputs(N, n) for (_, _, N, n) in inputs]
-
-    def digest(o):
-        h = hashlib.sha256()
-        for t in o:
-            h.update(t.numpy().tobytes())
-        return h.hexdigest()
-
-    digests = []
     for (w, lt, N, n), o in zip(inputs, outs):
         t0 = time.perf_counter()
         ctx.build(w, lt, *o)
         service.append(time.perf_counter() - t0)
-        digests.append(digest(o))
-        for t in o:
-            t.zero_()
-    ctx.close()
+    alone_ok = check_and_clear()
     capacity = len(service) / sum(service)  # requests per second
-    rate = 0.8 * capacity
-    rng = np.random.default_rng(5)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(inputs)))
-    done, lat_plain = 0.0, []
-    for a, sv in zip(arrivals, service):
-        start = max(a, done)
-        done = start + sv
-        lat_plain.append((done - a) * 1e3)
-    plain_span = done - arrivals[0]
 
-    # Served: real-time submission at the arrival times.
-    outs2 = outs
-    srv = binding.Server(device=0, budget_bytes=int(args.budget_gb * (1 << 30)) or (120 << 30), workers=3)
-    warm_t = srv.submit(inputs[0][0], inputs[0][1], *outputs(inputs[0][2], inputs[0][3]))
-    srv.wait(warm_t)
-    tickets = [None] * len(inputs)
-    t0 = time.perf_counter()
+    def plain_run(arrivals):
+        """The plain loop under an arrival trace, in real time."""
+        q = collections.deque()
+        cv = threading.Condition()
+        lat = [0.0] * len(inputs)
+        t0 = time.perf_counter()
 
-    def submitter():
-        for i, ((w, lt, N, n), o) in enumerate(zip(inputs, outs2)):
-            delay = arrivals[i] - arrivals[0] - (time.perf_counter() - t0)
+        def submitter():
+            for i in range(len(inputs)):
+                delay = arrivals[i] - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+                with cv:
+                    q.append(i)
+                    cv.notify()
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        for _ in range(len(inputs)):
+            with cv:
+                while not q:
+                    cv.wait()
+                i = q.popleft()
+            w, lt, _, _ = inputs[i]
+            ctx.build(w, lt, *outs[i])
+            lat[i] = (time.perf_counter() - t0 - arrivals[i]) * 1e3
+        th.join()
+        return lat, time.perf_counter() - t0
+
+    srv = binding.Server(device=0, budget_bytes=budget or (120 << 30), workers=3)
+    warm = srv.submit(inputs[0][0], inputs[0][1], *outs[0])
+    srv.wait(warm)
+    check_and_clear()
+
+    def served_run(arrivals):
+        tickets = [None] * len(inputs)
+        t0 = time.perf_counter()
+        for i, ((w, lt, N, n), o) in enumerate(zip(inputs, outs)):
+            delay = arrivals[i] - (time.perf_counter() - t0)
             if delay > 0:
                 time.sleep(delay)
             tickets[i] = srv.submit(w, lt, *o)
+        for t in tickets:
+            srv.wait(t)
+        span = time.perf_counter() - t0
+        return [srv.times(t)[1] for t in tickets], span
 
-    th = threading.Thread(target=submitter)
-    th.start()
-    th.join()
-    for t in tickets:
-        srv.wait(t)
-    span = time.perf_counter() - t0
-    lat_served = [srv.times(t)[1] for t in tickets]
-    counters = srv.counters()
-    srv.close()
-    # Every served result equals the plain loop's (the same build alone).
-    same = all(digest(o) == d for o, d in zip(outs2, digests))
     p = lambda xs, q: float(np.percentile(np.asarray(xs), q))
-    line = {"metric": METRIC, "value": total_bases / span / 1e9, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
-            "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic",
-            "config": {"workload": f"served: {len(inputs)} requests, {total_bases:,} bases, Poisson arrivals at "
-                                   f"{rate:.1f}/s (0.8x the plain loop's {capacity:.1f}/s)", "workers": 3,
-                       "packs": counters["packs"]},
-            "served": {"p50_ms": p(lat_served, 50), "p99_ms": p(lat_served, 99),
-                       "gbase_per_s": total_bases / span / 1e9},
-            "plain_loop": {"p50_ms": p(lat_plain, 50), "p99_ms": p(lat_plain, 99),
-                           "gbase_per_s": total_bases / plain_span / 1e9},
-            "results_identical_to_alone": same}
+    loads = {}
+    for j, f in enumerate((0.5, 0.8, 1.0, 1.5)):
+        trace_seed = 50 + j
+        rng = np.random.default_rng(trace_seed)
+        gaps = rng.exponential(1.0 / (f * capacity), size=len(inputs))
+        arrivals = np.cumsum(gaps) - gaps[0]  # the first request arrives at time 0
+        lat_p, span_p = plain_run(arrivals)
+        ok_p = check_and_clear()
+        before = srv.counters()["packs"]
+        lat_s, span_s = served_run(arrivals)
+        ok_s = check_and_clear()
+        loads[f"{f:g}x"] = {
+            "arrival_rate_per_s": f * capacity, "trace_seed": trace_seed,
+            "plain_loop": {"p50_ms": p(lat_p, 50), "p99_ms": p(lat_p, 99), "gbase_per_s": total_bases / span_p / 1e9,
+                           "span_s": span_p, "results_equal_oracle": ok_p},
+            "served": {"p50_ms": p(lat_s, 50), "p99_ms": p(lat_s, 99), "gbase_per_s": total_bases / span_s / 1e9,
+                       "span_s": span_s, "packs": srv.counters()["packs"] - before, "results_equal_oracle": ok_s}}
+    srv.close()
+    ctx.close()
+    sat = loads["1.5x"]
+    line = {"metric": METRIC, "value": sat["served"]["gbase_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": sat["served"]["span_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"served: {len(inputs)} requests, {total_bases:,} bases, Poisson arrivals at 0.5, "
+                                   f"0.8, 1.0 and 1.5x the plain loop's measured {capacity:.1f} requests/s",
+                       "workers": 3, "value": "served Gbase/s at 1.5x (saturated)"},
+            "loads": loads, "plain_alone_equal_oracle": alone_ok, "oracle_digests": want is not None}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -649,16 +736,23 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cxbwt", choices=["cxbwt", "reference"])
-    ap.add_argument("--cpu-sample-reads", type=int, default=500_000)
+    ap.add_argument("--cpu-sample-reads", type=int, default=None,
+                    help="reads of the CPU samples (default: 15 draw chunks, 1,966,080 reads, for the benchmark's "
+                         "cpu_baseline; 4 chunks, 524,288 reads, per step of the reference arm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-config2", action="store_true", help="skip the genome-like measurement (config2 key)")
     ap.add_argument("--reads", type=int, default=0,
                     help="reads per GPU (0: the workload's own size; smaller only for profiling captures)")
-    ap.add_argument("--workload", default="genome-like", choices=sorted(WORKLOADS) + ["batch", "serve", "length", "parts"],
-                    help="genome-like is the benchmark; the others are parity-test workloads timed for reference")
+    ap.add_argument("--workload", default="repeat-rich", choices=sorted(WORKLOADS) + ["batch", "serve", "length", "parts"],
+                    help="repeat-rich is the benchmark; the others are the other workloads, timed for reference")
+    ap.add_argument("--plan-flags", type=int, default=0,
+                    help="CXBWT_PLAN_* bits of the benchmark's contexts (1: 64-bit ids; for profiling captures)")
     ap.add_argument("--budget-gb", type=float, default=0.0,
                     help="device budget of the library context (0: 90%% of free memory)")
     args = ap.parse_args()
     rank, world, local = dist_env()
+    if args.cpu_sample_reads is None:
+        args.cpu_sample_reads = (4 if args.impl == "reference" else 15) * SAMPLE_CHUNK
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if args.workload == "batch":
@@ -673,21 +767,75 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_1401_7457_gb300 import binding, build, synth
+    from paper_1401_7457_gb300 import build
 
     if world > 1:
         dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     build.build()
+    args.warmup = max(args.warmup, 3)  # at least three untimed warm-up builds
 
     # Each rank builds its own independent collection (weak scaling, no data-path collective).
     desc, codes, lens = load_workload(args.workload, rank, args.reads)
+    res = measure(args, dist, world, local, dev, desc, codes, lens, args.steps, e2e_steps=max(3, min(args.steps, 10)))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        threads = os.cpu_count() or 1
+        rate, dt, sb = cpu_oracle_rate(codes, lens, args.cpu_sample_reads, threads)
+        n_s = min(args.cpu_sample_reads, lens.size)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "cpu_model": cpu_model(), "kind": "oracle",
+               "sample": f"first {n_s:,} reads ({sb:,} bases) of the workload, {dt:.1f} s wall"}
+        # The same oracle on one core, on a smaller sample (a few seconds).
+        n1 = max(1, args.cpu_sample_reads // 15)
+        rate1, dt1, sb1 = cpu_oracle_rate(codes, lens, n1, 1)
+        cpu["single_thread"] = {"value": rate1, "unit": UNIT, "cores": 1,
+                                "sample": f"first {min(n1, lens.size):,} reads ({sb1:,} bases), {dt1:.1f} s wall"}
+    del codes, lens
+
+    config2 = None
+    if args.workload != "genome-like" and not args.no_config2:
+        # The genome-like collection (1M x 100 bp at 20x, one slice, 32-bit ids), measured the same way.
+        d2, c2, l2 = load_workload("genome-like", rank, 0)
+        r2 = measure(args, dist, world, local, dev, d2, c2, l2, min(args.steps, 20), e2e_steps=max(3, min(args.steps, 10)))
+        config2 = {k: r2[k] for k in ("value", "unit", "ms_per_step", "config", "roofline", "phases", "e2e",
+                                      "gpu_launches_per_step", "clocks", "detail")}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u64" if res["detail"]["id_bytes"] == 8 else "u32",
+                "data": "synthetic", "config": res["config"], "roofline": res["roofline"], "phases": res["phases"],
+                "cpu_baseline": cpu, "e2e": res["e2e"], "gpu_launches": res["gpu_launches"],
+                "gpu_launches_per_step": res["gpu_launches_per_step"], "clocks": res["clocks"],
+                "detail": res["detail"]}
+        if config2 is not None:
+            line["config2"] = config2
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def measure(args, dist, world, local, dev, desc, codes, lens, steps, e2e_steps):
+    """One workload: K device-resident builds timed with CUDA events (and
+    their phases, from the library's own events), then e2e_steps builds
+    through the C ABI with pinned host buffers.  Returns the parts of a
+    benchmark line."""
+    import torch
+
+    from paper_1401_7457_gb300 import binding
+
     words = binding.pack_codes(codes)
     n = lens.size
     bases = int(lens.sum())
     N = bases + n
     n_words = (N + 15) // 16
+    read_len = int(lens[0])
+    budget = int(args.budget_gb * (1 << 30))
 
     d_words = torch.from_numpy(words.view(np.int32)).to(dev)
     d_lens = torch.from_numpy(lens.view(np.int32)).to(dev)
@@ -697,22 +845,21 @@ def main():
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    ctx = binding.Context(device=local, timing=True, budget_bytes=int(args.budget_gb * (1 << 30)))
+    ctx = binding.Context(device=local, timing=True, budget_bytes=budget, plan_flags=args.plan_flags)
 
     def step():
         ctx.build(d_words, d_lens, d_bwt, d_dpos, d_cnt, stream=stream)
 
-    args.warmup = max(args.warmup, 3)  # at least three untimed warm-up builds
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     ctx.reset_stats()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(nvml_id(dev)) as clocks:
-        for i in range(args.steps):
+        for i in range(steps):
             flush.fill_(i & 0xFF)  # evict the previous step's data from L2 (outside the events)
             ev[i][0].record(stream)
             step()
@@ -722,40 +869,44 @@ def main():
         dist.barrier()
     ms = [a.elapsed_time(b) for a, b in ev]
     st = ctx.stats()
-    value, total_ms = aggregate(dist, sum(ms), bases, world, args.steps)
+    ctx.close()
+    del ctx
+    value, total_ms = aggregate(dist, sum(ms), bases, world, steps)
 
-    # Dominant kernel: the onesweep digit pass.  Its algorithmic bytes per
-    # item are the key (4 B) and the id (4 or 8 B), read and written.
-    idb = id_bytes(n, int(lens.max()), int((int(lens.sum()) + 15) // 16) * 4)
+    # Dominant kernel: the onesweep digit pass that loads the key window the
+    # previous pass carried.  Its algorithmic bytes per item are the key
+    # (4 B) and the id (4 or 8 B), read and written; each launch is timed
+    # between its own events on the build stream.
+    idb = 8 if args.plan_flags & 1 else id_bytes(n, int(lens.max()), int((bases + 15) // 16) * 4)
     bytes_per_item = 2 * (4 + idb)
-    launches = max(st["sort_pass_launches"], 1)
-    pass_ms = st["sort_pass_ms"] / launches
-    items_per_launch = st["sort_pass_items"] / launches  # N per launch for a one-slice build
+    launches = max(st["carried_pass_launches"], 1)
+    pass_ms = st["carried_pass_ms"] / launches
+    items_per_launch = st["carried_pass_items"] / launches
     achieved = bytes_per_item * items_per_launch / (pass_ms * 1e-3) / 1e9 if pass_ms > 0 else 0.0
     peak, peak_kind = peak_hbm()
-    # The committed ncu summary covers 32-bit ids.
-    traffic_per_item = profiled_traffic() if idb == 4 else None
+    traffic_per_item = profiled_traffic(idb)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None if traffic_per_item is None else traffic_per_item * items_per_launch,
                 "peak_source": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s",
-                "kernel": "k_onesweep (LSD digit pass)", "launches_per_step": st["sort_pass_launches"] / args.steps,
+                "kernel": "k_onesweep, carried-key digit pass",
+                "launches_per_step": st["carried_pass_launches"] / steps,
+                "bytes_per_item": bytes_per_item, "items_per_launch": items_per_launch,
                 "algorithmic_bytes_per_launch": bytes_per_item * items_per_launch,
                 "avg_launch_ms": pass_ms, "frac_of_nominal_8tbs": achieved / 8000.0}
-    launches_per_step = st["kernel_launches"] / args.steps
 
     # End to end through the C ABI with pinned host buffers (copies inside the timed region).
     h_words = torch.from_numpy(words.view(np.int32)).pin_memory()
     h_lens = torch.from_numpy(lens.view(np.int32)).pin_memory()
+    del words, d_words, d_lens
     h_bwt = torch.empty(n_words, dtype=torch.int32).pin_memory()
     h_dpos = torch.empty(n, dtype=torch.int64).pin_memory()
     h_cnt = torch.zeros(5, dtype=torch.int64).pin_memory()
-    ctx2 = binding.Context(device=local, budget_bytes=int(args.budget_gb * (1 << 30)))
+    ctx2 = binding.Context(device=local, budget_bytes=budget, plan_flags=args.plan_flags)
     for _ in range(2):
         ctx2.build(h_words, h_lens, h_bwt, h_dpos, h_cnt, stream=stream)
     ctx2.reset_stats()
     torch.cuda.synchronize()
-    e2e_steps = max(3, min(args.steps, 10))
     t_e2e = []
     for _ in range(e2e_steps):
         flush.fill_(1)
@@ -764,52 +915,32 @@ def main():
         ctx2.build(h_words, h_lens, h_bwt, h_dpos, h_cnt, stream=stream)  # synchronous: returns with outputs on host
         t_e2e.append(time.perf_counter() - t0)
     st2 = ctx2.stats()
+    ctx2.close()
     e2e_value, e2e_ms = aggregate(dist, sum(t_e2e) * 1e3, bases, world, e2e_steps)
-    e2e_total = e2e_ms * 1e-3
     e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": st2["h2d_bytes"] // e2e_steps, "d2h_bytes_per_step": st2["d2h_bytes"] // e2e_steps,
-           "ms_per_step": e2e_total / e2e_steps * 1e3, "steps": e2e_steps}
-    ctx2.close()
+           "ms_per_step": e2e_ms / e2e_steps, "steps": e2e_steps,
+           "path": "cxbwt_build with pinned host input, lengths and outputs (BWT streamed per slice)"}
+    del h_words, h_lens, h_bwt, h_dpos, h_cnt, d_bwt, d_dpos, d_cnt, flush
+    torch.cuda.empty_cache()
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        threads = os.cpu_count() or 1
-        rate, dt, sb = cpu_oracle_rate(codes, lens, args.cpu_sample_reads, threads)
-        cpu = {"value": rate, "unit": UNIT, "cores": threads, "cpu_model": cpu_model(), "kind": "oracle",
-               "sample": f"first {min(args.cpu_sample_reads, n):,} reads ({sb:,} bases) of the workload, "
-                         f"{dt:.1f} s wall"}
-        # The same oracle on one core, on a smaller sample (a few seconds).
-        n1 = max(1, args.cpu_sample_reads // 5)
-        rate1, dt1, sb1 = cpu_oracle_rate(codes, lens, n1, 1)
-        cpu["single_thread"] = {"value": rate1, "unit": UNIT, "cores": 1,
-                                "sample": f"first {min(n1, n):,} reads ({sb1:,} bases), {dt1:.1f} s wall"}
-
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-                "config": {"workload": desc.format(n=n, N=N), "n_reads": n, "read_len": int(lens[0]), "bases_per_gpu": bases,
-                           "suffixes_per_gpu": N, "l2": "flushed between steps (512 MB write outside the events)",
-                           "input": "device-resident (HBM) before the timed region; outputs left in HBM"},
-                "roofline": roofline, "phases": phase_rates(st, args.steps, n, bases, idb, peak),
-                "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(st["kernel_launches"]), "gpu_launches_per_step": launches_per_step,
-                "clocks": clocks.summary(),
-                "detail": {"step_ms": ms, "slices_per_step": st["slices"] / args.steps,
-                           "sort_pass_ms_per_step": st["sort_pass_ms"] / args.steps,
-                           "group_finish_ms_per_step": st["group_ms"] / args.steps,
-                           "emit_ms_per_step": st["emit_ms"] / args.steps,
-                           "build_ms_per_step_lib": st["build_ms"] / args.steps,
-                           "id_bytes": idb,
-                           "cta_groups_per_step": st["cta_groups"] / args.steps,
-                           "big_groups_per_step": st["big_groups"] / args.steps}}
-        print(json.dumps(line), flush=True)
-    ctx.close()
-    if world > 1:
-        dist.destroy_process_group()
-    return 0
+    return {"value": value, "unit": UNIT, "ms_per_step": total_ms / steps,
+            "config": {"workload": desc.format(n=n, N=N), "n_reads": n, "read_len": read_len, "bases_per_gpu": bases,
+                       "suffixes_per_gpu": N, "l2": "flushed between steps (512 MB write outside the events)",
+                       "input": "device-resident (HBM) before the timed region; outputs left in HBM"},
+            "roofline": roofline, "phases": phase_rates(st, steps, n, bases, idb, peak), "e2e": e2e,
+            "gpu_launches": int(st["kernel_launches"]), "gpu_launches_per_step": st["kernel_launches"] / steps,
+            "clocks": clocks.summary(),
+            "detail": {"step_ms": ms, "slices_per_step": st["slices"] / steps,
+                       "digit_passes_per_step": st["sort_pass_launches"] / steps,
+                       "sort_pass_ms_per_step": st["sort_pass_ms"] / steps,
+                       "carried_pass_ms_per_step": st["carried_pass_ms"] / steps,
+                       "group_finish_ms_per_step": st["group_ms"] / steps,
+                       "emit_ms_per_step": st["emit_ms"] / steps,
+                       "build_ms_per_step_lib": st["build_ms"] / steps,
+                       "id_bytes": idb,
+                       "cta_groups_per_step": st["cta_groups"] / steps,
+                       "big_groups_per_step": st["big_groups"] / steps}}
 
 
 if __name__ == "__main__":

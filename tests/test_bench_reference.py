@@ -28,9 +28,9 @@ def test_reference_arm_json_line():
     assert line["higher_is_better"] is True and line["scaling"] == "weak" and line["vs_baseline"] is None
     assert line["data"] == "synthetic"
     assert line["value"] > 0 and line["ms_per_step"] > 0
-    # The same workload string as the cxbwt arm's benchmark line.
-    desc, _, lens = bench.load_workload("genome-like", 0, 0)
-    assert line["config"]["workload"] == desc.format(n=lens.size, N=int(lens.sum()) + lens.size)
+    # The same workload string as the cxbwt arm's benchmark line (the
+    # repeat-rich collection, of which only the sample's reads are drawn).
+    assert line["config"]["workload"] == bench.WORKLOADS["repeat-rich"].format(n=50_000_000, N=5_050_000_000)
     cpu = line["cpu_baseline"]
     assert cpu["kind"] == "oracle" and cpu["value"] == line["value"] and cpu["unit"] == line["unit"]
     assert cpu["cores"] >= 1 and "2,000 reads" in cpu["sample"]
@@ -56,11 +56,16 @@ def test_phase_rates_against_each_phase_bytes():
     n, bases, steps = 1_000_000, 100_000_000, 2
     N = n + bases
     st = {"sort_pass_ms": 2 * 2.61, "group_ms": 2 * 1.69, "emit_ms": 2 * 0.37, "build_ms": 2 * 4.84,
-          "sort_pass_items": 2 * 4 * N}
+          "sort_pass_items": 2 * 4 * N, "carried_pass_ms": 2 * 1.9, "carried_pass_items": 2 * 3 * N, "slices": 2}
     ph = bench.phase_rates(st, steps, n, bases, 4, 6792.0)
-    assert set(ph) == {"digit_passes", "group_finish", "emission", "histograms_and_planning"}
+    assert set(ph) == {"digit_passes", "carried_passes", "generating_passes", "group_finish", "emission",
+                       "histograms_and_planning"}
     assert abs(ph["digit_passes"]["bytes_per_step"] - 16 * 4 * N) < 1
     assert abs(ph["digit_passes"]["gbs"] - 16 * 4 * N / 2.61e-3 / 1e9) < 1e-6
+    # One generating pass (ids and keys written, the store read) and three carried ones per build.
+    assert abs(ph["carried_passes"]["bytes_per_step"] - 16 * 3 * N) < 1
+    assert abs(ph["generating_passes"]["bytes_per_step"] - (8 * N + bases / 4)) < 1
+    assert abs(ph["generating_passes"]["ms_per_step"] - (2.61 - 1.9)) < 1e-9
     assert abs(ph["group_finish"]["bytes_per_step"] - 12 * N) < 1
     assert abs(ph["emission"]["bytes_per_step"] - (4 * N + N / 4 + 8 * n + bases / 4)) < 1
     assert abs(ph["histograms_and_planning"]["ms_per_step"] - (4.84 - 2.61 - 1.69 - 0.37)) < 1e-9

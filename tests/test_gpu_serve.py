@@ -62,11 +62,13 @@ def test_poll_and_bad_requests():
     codes, lens = synth.uniform_reads(1000, 100, 5)
     with binding.Server(device=0, workers=1) as srv:
         bwt = np.zeros((101_000 + 15) // 16, dtype=np.uint32)
-        t = srv.submit(binding.pack_codes(codes), lens, bwt)
+        dpos = np.zeros(1000, dtype=np.uint64)
+        cnt = np.zeros(5, dtype=np.uint64)
+        t = srv.submit(binding.pack_codes(codes), lens, bwt, dpos, cnt)
         srv.wait(t)
         assert srv.poll(t)
         with pytest.raises(binding.CxbwtError):
             srv.submit(binding.pack_codes(codes), np.zeros(3, dtype=np.uint32), bwt)
-    assert_same({"bwt": binding.unpack_ascii(bwt, oracle_of(codes, lens)["dollar_pos"], 101_000),
-                 "dollar_pos": oracle_of(codes, lens)["dollar_pos"], "counts": oracle_of(codes, lens)["counts"]},
+    # The server's own $ rows and counts, against the oracle's.
+    assert_same({"bwt": binding.unpack_ascii(bwt, dpos, 101_000), "dollar_pos": dpos, "counts": cnt},
                 oracle_of(codes, lens))
