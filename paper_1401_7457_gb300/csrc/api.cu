@@ -53,23 +53,28 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
   a.R = r.R;
   a.n_reads = uint32_t(pl.n);
   a.timeout_ns = c->opt.wait_limit_ms > 0 ? uint64_t(c->opt.wait_limit_ms) * 1000000ull : kTimeoutNs;
-  a.bucket_shift = 32 - r.bucket_bits;
-  a.bucket_lo = sl.lo;
-  a.bucket_hi = sl.hi;
+  a.key_lo = sl.key_lo;
+  a.key_last = uint32_t(sl.key_hi - 1 - sl.key_lo);  // the offset of its last key (a part may span every key)
   const uint32_t d_sorted = std::min<uint32_t>(pl.D, 4 * (pl.w_last + 1));
 
   // ---- digit bases -----------------------------------------------------------
   // whole: rows 0..d_sorted-1 = char digits d, rows D.. = length digits.
   // slice: rows 0 = suffix length, 1..4 = window-0 digits (most significant first).
-  if (sl.whole) {
+  if (sl.pregen) {
+    // The slice's first windows are listed already: count their digits (rows 1..4).
+    CX_CUDA(c, cudaMemsetAsync(r.base + kRadix, 0, 4 * kRadix * 4, st));
+    CX_CUDA(c, launch_key_hist(r.keys[0], sl.rows, r.base + kRadix, c->sm_count, st));
+    r.launches += 2;
+  } else if (sl.whole) {
     CX_CUDA(c, cudaMemsetAsync(c->P.p, 0, uint64_t(pl.Lmax) * kRadix * 4, st));
     CX_CUDA(c, launch_poscount(r.R, uint32_t(pl.n), pl.Lmax, static_cast<uint32_t*>(c->P.p), c->sm_count, st));
     CX_CUDA(c, launch_digitbase(static_cast<const uint32_t*>(c->P.p), pl.Lmax, d_sorted, pl.uniform ? 1 : 0,
                                 uint32_t(pl.n), pl.Lmax, static_cast<const uint32_t*>(c->lenhist.p), r.base, st));
     r.launches += 2;
   } else {
-    CX_CUDA(c, cudaMemsetAsync(r.base, 0, 5 * kRadix * 4, st));
-    CX_CUDA(c, launch_pass_hist(r.R, uint32_t(pl.n), r.bucket_bits, sl.lo, sl.hi, r.base, c->sm_count, st));
+    CX_CUDA(c, cudaMemsetAsync(r.base, 0, 6 * kRadix * 4, st));
+    CX_CUDA(c, launch_pass_hist(r.R, uint32_t(pl.n), sl.key_lo, uint32_t(sl.key_hi - 1 - sl.key_lo), r.base,
+                                c->sm_count, st));
     r.launches += 2;
   }
   auto digit_base = [&](uint32_t d) -> const uint32_t* {  // char digit d of window 0 (or any window when whole)
@@ -81,10 +86,47 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
   int cur = 0, kin = 0;
   const int idb = pl.idb;
   bool first = pl.uniform;  // the first digit pass generates the start order
+  bool listed = sl.pregen;  // window 0 is already in the key array, in (length, read) order
   a.n_gen = pl.N;  // generated passes enumerate every suffix (a slice's pass filters them)
   a.n_out = sl.rows;
   a.n_tiles = uint32_t((pl.N + TILE - 1) / TILE);
-  if (!pl.uniform) {
+  if (!pl.uniform && !sl.whole) {
+    // A slice of a collection of mixed read lengths: every suffix listed in
+    // read-major order, the slice's kept with window 0, stably ordered by the
+    // low byte of the suffix length, then by its high byte.
+    a.vals_in = nullptr;
+    a.vals_out = r.vals[cur ^ 1];
+    a.keys_in = nullptr;
+    a.keys_out = r.keys[kin];
+    a.digit_base = r.base;  // row 0: low byte of the suffix length
+    a.key_shift = 0;
+    a.window_c0 = 0;
+    a.epoch = ++c->epoch;
+    if (tev) CX_TRY(pass_event_begin(c, r));
+    CX_CUDA(c, launch_onesweep(a, kSrcInitMixed, true, true, idb, r.shape, st));
+    if (tev) CX_TRY(pass_event_end(c, r, 0));
+    cur ^= 1;
+    ++r.sort_launches;
+    r.sort_items += sl.rows;
+    if (pl.Lmax > 255) {
+      a.n_gen = sl.rows;
+      a.n_tiles = uint32_t((uint64_t(sl.rows) + TILE - 1) / TILE);
+      a.vals_in = r.vals[cur];
+      a.vals_out = r.vals[cur ^ 1];
+      a.keys_in = r.keys[kin];
+      a.keys_out = r.keys[kin ^ 1];
+      a.digit_base = r.base + 5 * size_t(kRadix);  // row 5: high byte of the suffix length
+      a.key_shift = 8;
+      a.epoch = ++c->epoch;
+      CX_CUDA(c, launch_onesweep(a, kSrcCarriedLength, true, false, idb, r.shape, st));
+      cur ^= 1;
+      kin ^= 1;
+      ++r.sort_launches;
+      r.sort_items += sl.rows;
+    }
+    listed = true;
+    first = false;
+  } else if (!pl.uniform) {
     // Mixed lengths (whole collection only): id list in read order, then
     // stable passes over the suffix length.
     CX_CUDA(c, launch_identity(r.R, uint32_t(pl.n), r.vals[0], idb, st));
@@ -105,7 +147,7 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
       ++r.sort_launches;
       r.sort_items += sl.rows;
     }
-  } else if (r.read_major) {
+  } else if (r.read_major && !sl.pregen) {
     // Read-major generated order (the store is read in address order),
     // filtered to the slice, stably sorted by suffix length, window 0 carried.
     a.vals_in = nullptr;
@@ -118,7 +160,7 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
     a.epoch = ++c->epoch;
     if (tev) CX_TRY(pass_event_begin(c, r));
     CX_CUDA(c, launch_onesweep(a, kSrcInitReadMajor, true, !sl.whole, idb, r.shape, st));
-    if (tev) CX_TRY(pass_event_end(c, r, false));
+    if (tev) CX_TRY(pass_event_end(c, r, 0));
     cur ^= 1;
     ++r.sort_launches;
     r.sort_items += sl.rows;
@@ -130,7 +172,7 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
     for (int64_t d = d_hi; d >= int64_t(d_lo); --d) {
       const bool first_in_window = (uint32_t(d) == d_hi);
       const bool last_in_window = (uint32_t(d) == d_lo);
-      const bool carried = !first_in_window || (w == 0 && r.read_major && pl.uniform);
+      const bool carried = !first_in_window || (w == 0 && (listed || (r.read_major && pl.uniform)));
       const int mode = carried ? kSrcCarried : (first ? kSrcInitUniform : kSrcExtract);
       // The group plan keeps the window-0 keys of the final order: groups are runs of equal keys.
       const bool write_key = !last_in_window || pl.groups;
@@ -149,7 +191,7 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
       a.stall_tile0 = (c->opt.plan_flags & CXBWT_PLAN_TEST_STALL) && r.sort_launches == 0 ? 1u : 0u;
       if (tev) CX_TRY(pass_event_begin(c, r));
       CX_CUDA(c, launch_onesweep(a, mode, write_key, generated && !sl.whole, idb, r.shape, st));
-      if (tev) CX_TRY(pass_event_end(c, r, mode == kSrcCarried));
+      if (tev) CX_TRY(pass_event_end(c, r, mode == kSrcCarried ? 1 : 0));
       a.stall_tile0 = 0;
       if (mode == kSrcCarried) {
         ++r.carried_launches;
@@ -180,7 +222,7 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
     g.big_cap = uint32_t(big_cap);
     g.counts = r.d_seg;
     g.err = r.d_err;
-    CX_CUDA(c, launch_segsort(g, pl.seg_words, idb, c->sm_count, st));
+    CX_CUDA(c, launch_segsort(g, pl.seg_words, idb, c->sm_count, pl.n_words * 4 > (64u << 20), st));
     r.launches += 2;
     // Remainders too large for one CTA (rare: long runs of equal bases) are
     // finished here with LSD passes over bases 16.. restricted to their rows.
@@ -238,6 +280,68 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
     }
   }
   *cur_out = cur;
+  return CXBWT_OK;
+}
+
+// The one generating pass of a build in several slices of 4-base buckets:
+// every suffix is listed, in read-major order with its first window, into
+// its slice's part of r.vals[0] / r.keys[0] (slice s at rows [row0_s,
+// row0_s + rows_s)), stably ordered by suffix length inside the slice, which
+// with the read-major order gives the (suffix length, read) start order the
+// slice's window passes need.  The digit is (slice, suffix length); its
+// first output rows follow from the per-position 4-mer counts P that planned
+// the slices: suffix (i, k) has length L - k and first 4 bases = the 4-mer of
+// read i at position k, and the n terminator-only suffixes fall in bucket 0.
+int split_pass(cxbwt_ctx* c, Run& r, const std::vector<Slice>& slices, const std::vector<uint32_t>& P, bool timing) {
+  const Plan& pl = r.pl;
+  const uint32_t L = pl.Lmax, L1 = L + 1, S = uint32_t(slices.size());
+  std::vector<uint8_t> split_of(kRadix, 0);
+  for (uint32_t si = 0; si < S; ++si)
+    for (uint64_t b = slices[si].key_lo >> 24; b < (slices[si].key_hi >> 24); ++b) split_of[b] = uint8_t(si);
+  std::vector<uint64_t> cnt(size_t(S) * L1, 0);
+  cnt[size_t(split_of[0]) * L1] += pl.n;
+  for (uint32_t t = 1; t <= L; ++t)
+    for (int v = 0; v < kRadix; ++v) cnt[size_t(split_of[v]) * L1 + t] += P[size_t(L - t) * kRadix + v];
+  std::vector<uint32_t> sbase(kRadix, 0);
+  for (uint32_t si = 0; si < S; ++si) {
+    uint64_t acc = 0;
+    for (uint32_t t = 0; t < L1; ++t) {
+      sbase[si * L1 + t] = uint32_t(acc);
+      acc += cnt[size_t(si) * L1 + t];
+    }
+    if (acc != slices[si].rows)
+      return fail(c, CXBWT_EINTERNAL, "slice %u: %llu listed suffixes, %u planned", si, (unsigned long long)acc,
+                  slices[si].rows);
+  }
+  uint32_t* d_sbase = r.base + size_t(std::max<uint32_t>(pl.D + pl.len_passes, 5)) * kRadix;
+  uint8_t* d_split = reinterpret_cast<uint8_t*>(d_sbase + kRadix);
+  CX_CUDA(c, cudaMemcpyAsync(d_sbase, sbase.data(), kRadix * 4, cudaMemcpyHostToDevice, r.st));
+  CX_CUDA(c, cudaMemcpyAsync(d_split, split_of.data(), kRadix, cudaMemcpyHostToDevice, r.st));
+  const uint32_t TILE = uint32_t(r.shape.tile());
+  PassArgs a{};
+  a.status = static_cast<unsigned long long*>(c->status.p);
+  a.tile_counter = r.d_counter;
+  a.err = r.d_err;
+  a.R = r.R;
+  a.n_reads = uint32_t(pl.n);
+  a.timeout_ns = c->opt.wait_limit_ms > 0 ? uint64_t(c->opt.wait_limit_ms) * 1000000ull : kTimeoutNs;
+  a.n_gen = pl.N;
+  a.n_out = 0;  // every row goes to a slice's own arrays
+  a.n_tiles = uint32_t((pl.N + TILE - 1) / TILE);
+  a.digit_base = d_sbase;
+  a.split_of = d_split;
+  for (uint32_t si = 0; si < S; ++si) {
+    a.split_vals[si] = vptr(c->vals[0].p, pl.idb, slices[si].row0);
+    a.split_keys[si] = static_cast<uint32_t*>(c->keys[0].p) + slices[si].row0;
+    a.split_rows[si] = slices[si].rows;
+  }
+  a.epoch = ++c->epoch;
+  if (timing) CX_TRY(pass_event_begin(c, r));
+  CX_CUDA(c, launch_onesweep(a, kSrcInitSplit, true, false, pl.idb, r.shape, r.st));
+  if (timing) CX_TRY(pass_event_end(c, r, 2));
+  ++r.sort_launches;
+  r.sort_items += pl.N;
+  r.read_major = true;
   return CXBWT_OK;
 }
 
@@ -432,15 +536,13 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   m1 = std::min<uint64_t>(m1 > (64u << 20) ? m1 - (1u << 20) : (m1 > 32768 ? m1 - 16384 : m1), 0xFFFFFFF0ull);
   std::vector<Slice> slices;
   uint64_t part_row0 = 0, part_rows = pl.N;  // global rows this call emits
+  std::vector<uint32_t> P_host;  // per-position 4-mer counts, when the slices were planned from them
+  bool refined = false;          // an 8-base bucket was split into 16-base ones
   if (pl.N <= m1 && !part) {
     Slice sl;
     sl.rows = uint32_t(pl.N);
     slices.push_back(sl);
   } else {
-    if (!pl.uniform)
-      return fail(c, CXBWT_EUNSUPPORTED, part ? "bucket-range parts need reads of one length"
-                                              : "collections of mixed read lengths must fit one slice (%llu suffixes, %llu fit)",
-                  (unsigned long long)pl.N, (unsigned long long)m1);
     if (!pl.groups)
       return fail(c, CXBWT_EUNSUPPORTED, "device-memory-bounded slices and parts use the group plan (reads of at most 528 bases)");
     // Figure 2 step 1: suffixes per bucket; then consecutive buckets packed
@@ -456,7 +558,8 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
       CX_CUDA(c, cudaMemsetAsync(c->P.p, 0, uint64_t(pl.Lmax) * kRadix * 4, st));
       CX_CUDA(c, launch_poscount(r.R, uint32_t(n), pl.Lmax, static_cast<uint32_t*>(c->P.p), c->sm_count, st));
       ++r.launches;
-      std::vector<uint32_t> P(size_t(pl.Lmax) * kRadix);
+      std::vector<uint32_t>& P = P_host;
+      P.resize(size_t(pl.Lmax) * kRadix);
       CX_CUDA(c, cudaMemcpyAsync(P.data(), c->P.p, P.size() * 4, cudaMemcpyDeviceToHost, st));
       CX_CUDA(c, cudaStreamSynchronize(st));
       r.d2h += P.size() * 4;
@@ -498,25 +601,68 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
     uint64_t row = 0, acc = 0;
     for (uint32_t b = 0; b < b_lo; ++b) row += bh[b];
     part_row0 = row;
-    uint32_t lo = b_lo;
-    for (uint32_t b = b_lo; b <= b_hi; ++b) {
-      const bool end = (b == b_hi);
-      const uint64_t cnt = end ? 0 : bh[b];
-      if (!end && cnt > m1)
-        return fail(c, CXBWT_ENOMEM, "one %u-base bucket holds %llu suffixes, more than the %llu a slice can hold",
-                    r.bucket_bits / 2, (unsigned long long)cnt, (unsigned long long)m1);
-      if (end || acc + cnt > m1) {
+    // Units of consecutive first windows, in key order: the buckets, except
+    // that an 8-base bucket holding more suffixes than a slice is refined by
+    // its next 8 bases (Section 3.1: a partition larger than the GPU takes is
+    // split by the characters that follow its prefix) into 16-base units.
+    struct Unit {
+      uint64_t key_lo, key_hi, cnt;
+    };
+    std::vector<Unit> units;
+    const uint32_t ush = 32 - r.bucket_bits;
+    for (uint32_t b = b_lo; b < b_hi; ++b) {
+      if (bh[b] <= m1) {
+        units.push_back(Unit{uint64_t(b) << ush, uint64_t(b + 1) << ush, bh[b]});
+        continue;
+      }
+      if (r.bucket_bits != kBucketBits)
+        return fail(c, CXBWT_EINTERNAL, "a %u-base bucket exceeds a slice", r.bucket_bits / 2);
+      refined = true;
+      CX_TRY(ensure(c, c->bhist, (uint64_t(1) << kBucketBits) * 8, "bucket counts"));
+      CX_CUDA(c, cudaMemsetAsync(c->bhist.p, 0, (uint64_t(1) << kBucketBits) * 8, st));
+      CX_CUDA(c, launch_sub_bucket_hist(r.R, uint32_t(n), b, static_cast<unsigned long long*>(c->bhist.p), c->sm_count,
+                                        st));
+      ++r.launches;
+      std::vector<uint64_t> sub(size_t(1) << 16);
+      CX_CUDA(c, cudaMemcpyAsync(sub.data(), c->bhist.p, sub.size() * 8, cudaMemcpyDeviceToHost, st));
+      CX_CUDA(c, cudaStreamSynchronize(st));
+      r.d2h += sub.size() * 8;
+      uint64_t total = 0;
+      for (uint32_t x = 0; x < sub.size(); ++x) {
+        total += sub[x];
+        if (sub[x] > m1)
+          return fail(c, CXBWT_ENOMEM,
+                      "one 16-base prefix holds %llu suffixes, more than the %llu a slice can hold (refining by the "
+                      "bases after the first 16 is not built)",
+                      (unsigned long long)sub[x], (unsigned long long)m1);
+        units.push_back(Unit{(uint64_t(b) << 16) | x, ((uint64_t(b) << 16) | x) + 1, sub[x]});
+      }
+      if (total != bh[b])
+        return fail(c, CXBWT_EINTERNAL, "8-base bucket %u: %llu suffixes refined, %llu counted", b,
+                    (unsigned long long)total, (unsigned long long)bh[b]);
+    }
+    // Slices of about equal size: as few as m1 allows, each closed once it
+    // reaches the average (smaller slices need less workspace).
+    uint64_t range_rows = 0;
+    for (const Unit& u : units) range_rows += u.cnt;
+    const uint64_t n_min = std::max<uint64_t>(1, (range_rows + m1 - 1) / std::max<uint64_t>(m1, 1));
+    const uint64_t target = (range_rows + n_min - 1) / n_min;
+    size_t lo = 0;
+    for (size_t u = 0; u <= units.size(); ++u) {
+      const bool end = (u == units.size());
+      const uint64_t cnt = end ? 0 : units[u].cnt;
+      if (end || acc + cnt > m1 || acc >= target) {
         if (acc) {
           Slice sl;
           sl.whole = false;
-          sl.lo = lo;
-          sl.hi = b;
+          sl.key_lo = uint32_t(units[lo].key_lo);
+          sl.key_hi = units[u - 1].key_hi;
           sl.rows = uint32_t(acc);
           sl.row0 = row;
           slices.push_back(sl);
           row += acc;
         }
-        lo = b;
+        lo = u;
         acc = 0;
       }
       acc += cnt;
@@ -564,10 +710,26 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   for (const Slice& sl : slices) max_rows = std::max(max_rows, sl.rows);
   const uint64_t gen_tiles = (pl.N + TILE - 1) / TILE;
 
+  // A build in a few slices of 4-base buckets lists every slice in one
+  // generating pass (kSrcInitSplit: digit = (slice, suffix length)) into its
+  // own part of one array of N rows, instead of one pass over all N suffixes
+  // per slice; each slice then sorts between its part and one spare array.
+  // That needs (N + largest slice) rows of ids and keys instead of twice the
+  // largest slice, so it is taken only when the budget holds them.
+  bool split = false;
+  if (!part && slices.size() > 1 && slices.size() <= kMaxSplit && pl.uniform && r.bucket_bits == 8 && !refined &&
+      !P_host.empty() && slices.size() * (pl.Lmax + 1) <= uint64_t(kRadix)) {
+    const uint64_t need = (pl.N + max_rows) * uint64_t(pl.idb + 4) +
+                          uint64_t(double(max_rows) * (8.0 / 33 + 8.0 / 1025)) +
+                          (out_sa && !sa_dev ? uint64_t(max_rows) * 8 : 0);
+    split = need <= avail;
+  }
+
   // ---- workspace ---------------------------------------------------------
-  CX_TRY(ensure(c, c->vals[0], uint64_t(max_rows) * pl.idb, "suffix ids"));
+  const uint64_t rows0 = split ? pl.N : uint64_t(max_rows);
+  CX_TRY(ensure(c, c->vals[0], rows0 * pl.idb, "suffix ids"));
   CX_TRY(ensure(c, c->vals[1], uint64_t(max_rows) * pl.idb, "suffix ids"));
-  CX_TRY(ensure(c, c->keys[0], uint64_t(max_rows) * 4, "keys"));
+  CX_TRY(ensure(c, c->keys[0], rows0 * 4, "keys"));
   CX_TRY(ensure(c, c->keys[1], uint64_t(max_rows) * 4, "keys"));
   const void* status_before = c->status.p;
   CX_TRY(ensure(c, c->status, gen_tiles * kRadix * 8, "look-back words"));
@@ -576,7 +738,9 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
     CX_CUDA(c, cudaMemsetAsync(c->status.p, 0, c->status.cap, st));
   }
   CX_TRY(ensure(c, c->P, uint64_t(pl.Lmax) * kRadix * 4, "position counts"));
-  CX_TRY(ensure(c, c->base, uint64_t(std::max<uint32_t>(pl.D + pl.len_passes, 5)) * kRadix * 4, "digit bases"));
+  // digit bases; then the split pass's digit bases and slice of every bucket (two more rows)
+  const uint32_t split_row = std::max<uint32_t>(pl.D + pl.len_passes, 5);
+  CX_TRY(ensure(c, c->base, uint64_t(split_row + 2) * kRadix * 4, "digit bases"));
   if (pl.uniform && !c->lenhist.p) CX_TRY(ensure(c, c->lenhist, 4, "length histogram"));
   if (pl.groups && pl.Lmax > 16) {
     CX_TRY(ensure(c, c->seglist, (cta_list_cap(max_rows) + big_list_cap(max_rows, pl.seg_words)) * 8, "group lists"));
@@ -597,7 +761,7 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
                                cudaMemcpyHostToDevice, st));
     h2d += len_bases.size() * 4;
   }
-  const uint64_t passes_max = uint64_t(slices.size()) * (pl.D + pl.len_passes + 1) + 4 * pl.W * 64;
+  const uint64_t passes_max = uint64_t(slices.size()) * (pl.D + pl.len_passes + 1) + 4 * pl.W * 64 + 1;
   if (uint64_t(c->epoch) + passes_max + 2 >= (uint64_t(1) << 30)) {
     // Look-back flags are 2*epoch and 2*epoch+1 in 32 bits: restart the epochs.
     CX_CUDA(c, cudaMemsetAsync(c->status.p, 0, c->status.cap, st));
@@ -615,11 +779,19 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
     CX_CUDA(c, cudaEventRecord(c->ev[0], st));
   }
 
+  if (split) CX_TRY(split_pass(c, r, slices, P_host, timing));
+
   uint64_t words_sent = 0;  // BWT words already streamed to the host
   for (size_t si = 0; si < slices.size(); ++si) {
-    const Slice& sl = slices[si];
+    Slice& sl = slices[si];
     int cur = 0;
     cudaEvent_t* tev = timing ? &c->tev[4 * si] : nullptr;
+    if (split) {
+      // The slice's part of the listed rows, and the spare array to sort into.
+      sl.pregen = true;
+      r.vals[0] = vptr(c->vals[0].p, pl.idb, sl.row0);
+      r.keys[0] = static_cast<uint32_t*>(c->keys[0].p) + sl.row0;
+    }
     CX_TRY(sort_slice(c, r, sl, &cur, tev));
     if (tev) CX_CUDA(c, cudaEventRecord(tev[2], st));
     // ---- emission of the slice -------------------------------------------
@@ -713,7 +885,8 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
       if (!r.pev_carried[j]) continue;
       float ms = 0;
       CX_CUDA(c, cudaEventElapsedTime(&ms, c->pev[2 * size_t(j)], c->pev[2 * size_t(j) + 1]));
-      c->stats.carried_pass_ms += ms;
+      if (r.pev_carried[j] == 1) c->stats.carried_pass_ms += ms;
+      else c->stats.sort_pass_ms += ms;  // the split pass runs before every slice
     }
     c->stats.build_ms += ms_all;
   }

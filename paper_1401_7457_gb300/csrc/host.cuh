@@ -194,9 +194,12 @@ inline void plan_ids(Plan& pl, bool force64, bool want_sym) {
 
 struct Slice {
   bool whole = true;          // every suffix (no bucket filter)
-  uint32_t lo = 0, hi = 0;    // bucket range when not whole
+  uint32_t key_lo = 0;        // when not whole: the suffixes whose first window (16 bases, A-padded)
+  uint64_t key_hi = 0;        //   lies in [key_lo, key_hi), a range of buckets of 4, 8 or 16 bases
   uint32_t rows = 0;          // suffixes in the slice
   uint64_t row0 = 0;          // global BWT row of its first suffix
+  bool pregen = false;        // its ids and first windows are already listed, in (length, read) order, in
+                              // r.vals[0] / r.keys[0] (the split pass of a build in several slices)
 };
 
 // A bucket-range part of a build (Section 3.3): only the suffixes whose first
@@ -235,7 +238,7 @@ struct Run {
   // Per-pass timing (timing option): pass j ran between events pev[2j] and
   // pev[2j+1]; pev_carried[j] says whether it was a carried-key pass.
   uint32_t n_pev = 0;
-  std::vector<uint8_t> pev_carried;
+  std::vector<uint8_t> pev_carried;  // 1: carried-key pass; 2: the split pass (outside every slice); 0: other
 };
 
 // Records the start event of one timed digit pass (grows the context's pool).
@@ -250,9 +253,9 @@ inline int pass_event_begin(cxbwt_ctx* c, Run& r) {
 }
 
 // Records the end event of the pass begun last.
-inline int pass_event_end(cxbwt_ctx* c, Run& r, bool carried) {
+inline int pass_event_end(cxbwt_ctx* c, Run& r, int kind) {
   CX_CUDA(c, cudaEventRecord(c->pev[2 * size_t(r.n_pev) + 1], r.st));
-  r.pev_carried.push_back(carried ? 1 : 0);
+  r.pev_carried.push_back(uint8_t(kind));
   ++r.n_pev;
   return CXBWT_OK;
 }

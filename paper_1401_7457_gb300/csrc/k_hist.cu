@@ -130,15 +130,40 @@ __global__ void __launch_bounds__(512) k_bucket_hist(const ReadIndex R, uint32_t
     if (sh[x]) atomicAdd(&hist[slab0 + x], (unsigned long long)sh[x]);
 }
 
-// Digit counts of the suffixes of one HBM-bounded pass (bucket in [lo, hi)),
-// every read of one length L: row 0 = suffix length (the read-major start
-// order's length digit), rows 1..4 = the four 8-bit digits of the first
-// window (most significant first).  Figure 2 step 3(a)'s rescan of all
-// suffixes for the selected partitions.
-__global__ void __launch_bounds__(512) k_pass_hist(const ReadIndex R, uint32_t n_reads, uint32_t bucket_bits,
-                                                   uint32_t lo, uint32_t hi, uint32_t* __restrict__ hist) {
-  __shared__ uint32_t sh[5 * kRadix];
-  for (uint32_t x = threadIdx.x; x < 5 * kRadix; x += blockDim.x) sh[x] = 0;
+// Suffixes of one 8-base bucket (first window >> 16 == prefix) per value of
+// their next 8 bases: when one 8-base bucket holds more suffixes than a
+// slice, Section 3.1 refines it by the characters that follow.  Same walk as
+// k_bucket_hist; CTAs own 16384-counter slabs of the 65536 sub-buckets.
+__global__ void __launch_bounds__(512) k_sub_bucket_hist(const ReadIndex R, uint32_t n_reads, uint32_t prefix,
+                                                         unsigned long long* __restrict__ hist) {
+  extern __shared__ uint32_t sh[];  // kBucketSlab counters
+  const uint32_t slab0 = blockIdx.y * kBucketSlab;
+  for (uint32_t x = threadIdx.x; x < kBucketSlab; x += blockDim.x) sh[x] = 0;
+  __syncthreads();
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_reads; i += gridDim.x * blockDim.x) {
+    Suffix s = decode(R, uint64_t(i) << R.shift);
+    const uint32_t L = s.len;
+    for (uint32_t k = 0; k <= L; ++k) {
+      s.k = k;
+      const uint32_t w = window16(R, s, 0);
+      if ((w >> 16) == prefix && (w & 0xFFFFu) - slab0 < kBucketSlab) atomicAdd(&sh[(w & 0xFFFFu) - slab0], 1u);
+    }
+  }
+  __syncthreads();
+  for (uint32_t x = threadIdx.x; x < kBucketSlab; x += blockDim.x)
+    if (sh[x]) atomicAdd(&hist[slab0 + x], (unsigned long long)sh[x]);
+}
+
+// Digit counts of the suffixes of one HBM-bounded pass (first window w with
+// w - key_lo <= key_last): row 0 = low byte of the suffix length (the
+// read-major start order's length digit), rows 1..4 = the four 8-bit digits
+// of the first window (most significant first), row 5 = high byte of the
+// suffix length.  Figure 2 step 3(a)'s rescan of all suffixes for the
+// selected partitions.
+__global__ void __launch_bounds__(512) k_pass_hist(const ReadIndex R, uint32_t n_reads, uint32_t key_lo,
+                                                   uint32_t key_last, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t sh[6 * kRadix];
+  for (uint32_t x = threadIdx.x; x < 6 * kRadix; x += blockDim.x) sh[x] = 0;
   __syncthreads();
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_reads; i += gridDim.x * blockDim.x) {
     Suffix s = decode(R, uint64_t(i) << R.shift);
@@ -146,16 +171,44 @@ __global__ void __launch_bounds__(512) k_pass_hist(const ReadIndex R, uint32_t n
     for (uint32_t k = 0; k <= L; ++k) {
       s.k = k;
       const uint32_t key = window16(R, s, 0);
-      if ((key >> (32 - bucket_bits)) - lo < hi - lo) {
-        atomicAdd(&sh[min(L - k, 255u)], 1u);
+      if (key - key_lo <= key_last) {
+        atomicAdd(&sh[(L - k) & 255u], 1u);
+        atomicAdd(&sh[5 * kRadix + ((L - k) >> 8)], 1u);
 #pragma unroll
         for (int j = 0; j < 4; ++j) atomicAdd(&sh[(1 + j) * kRadix + ((key >> (24 - 8 * j)) & 255u)], 1u);
       }
     }
   }
   __syncthreads();
-  for (uint32_t x = threadIdx.x; x < 5 * kRadix; x += blockDim.x)
+  for (uint32_t x = threadIdx.x; x < 6 * kRadix; x += blockDim.x)
     if (sh[x]) atomicAdd(&hist[x], sh[x]);
+}
+
+// Counts of the four 8-bit digits of n keys already in HBM (a slice's first
+// windows, written by the pass that listed it): 4 bytes read per key, where
+// a rescan of the store would decode and gather every suffix of the
+// collection again.  Each warp counts into its own shared copy.
+constexpr int kKeyHistThreads = 512;
+
+__global__ void __launch_bounds__(kKeyHistThreads) k_key_hist(const uint32_t* __restrict__ keys, uint64_t n,
+                                                              uint32_t* __restrict__ hist) {
+  extern __shared__ uint32_t sk[];  // [warps][4 * 256]
+  constexpr int kWarps = kKeyHistThreads / 32;
+  for (uint32_t x = threadIdx.x; x < kWarps * 4 * kRadix; x += blockDim.x) sk[x] = 0;
+  __syncthreads();
+  uint32_t* mine = sk + (threadIdx.x >> 5) * 4 * kRadix;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t r = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < n; r += stride) {
+    const uint32_t k = __ldg(keys + r);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) atomicAdd(&mine[j * kRadix + ((k >> (24 - 8 * j)) & 255u)], 1u);
+  }
+  __syncthreads();
+  for (uint32_t x = threadIdx.x; x < 4 * kRadix; x += blockDim.x) {
+    uint32_t sum = 0;
+    for (int w = 0; w < kWarps; ++w) sum += sk[w * 4 * kRadix + x];
+    if (sum) atomicAdd(&hist[x], sum);
+  }
 }
 
 __global__ void __launch_bounds__(kRadix) k_scan_rows(uint32_t* hist) {
@@ -235,15 +288,44 @@ cudaError_t launch_bucket_hist(const ReadIndex& R, uint32_t n_reads, uint32_t bu
   return cudaGetLastError();
 }
 
-cudaError_t launch_pass_hist(const ReadIndex& R, uint32_t n_reads, uint32_t bucket_bits, uint32_t lo, uint32_t hi,
+cudaError_t launch_sub_bucket_hist(const ReadIndex& R, uint32_t n_reads, uint32_t prefix, unsigned long long* hist,
+                                   int sm_count, cudaStream_t st) {
+  const uint32_t slabs = 65536u / kBucketSlab;
+  uint32_t gx = (n_reads + 511) / 512;
+  const uint32_t cap = max(1u, uint32_t(2 * sm_count) / slabs);
+  if (gx > cap) gx = cap;
+  if (gx == 0) gx = 1;
+  const int smem = int(kBucketSlab * sizeof(uint32_t));
+  cudaError_t e = cudaFuncSetAttribute(k_sub_bucket_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  k_sub_bucket_hist<<<dim3(gx, slabs), 512, smem, st>>>(R, n_reads, prefix, hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass_hist(const ReadIndex& R, uint32_t n_reads, uint32_t key_lo, uint32_t key_last,
                              uint32_t* hist, int sm_count, cudaStream_t st) {
   uint32_t gx = (n_reads + 511) / 512;
   if (gx > uint32_t(2 * sm_count)) gx = 2 * sm_count;
   if (gx == 0) gx = 1;
-  k_pass_hist<<<gx, 512, 0, st>>>(R, n_reads, bucket_bits, lo, hi, hist);
+  k_pass_hist<<<gx, 512, 0, st>>>(R, n_reads, key_lo, key_last, hist);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_scan_rows<<<5, kRadix, 0, st>>>(hist);
+  k_scan_rows<<<6, kRadix, 0, st>>>(hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_key_hist(const uint32_t* keys, uint64_t n, uint32_t* hist, int sm_count, cudaStream_t st) {
+  if (n > 0) {
+    const int smem = int(kKeyHistThreads / 32 * 4 * kRadix * sizeof(uint32_t));
+    cudaError_t e = cudaFuncSetAttribute(k_key_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    uint64_t gx = (n + kKeyHistThreads - 1) / kKeyHistThreads;
+    if (gx > uint64_t(2 * sm_count)) gx = 2 * sm_count;
+    k_key_hist<<<uint32_t(gx), kKeyHistThreads, smem, st>>>(keys, n, hist);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_scan_rows<<<4, kRadix, 0, st>>>(hist);
   return cudaGetLastError();
 }
 

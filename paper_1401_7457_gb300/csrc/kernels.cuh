@@ -26,8 +26,25 @@ enum SrcMode : int {
   // Ids are loaded; the digit is the index of the id's collection in a batch
   // pack (coll_start: first read of each collection, ascending).
   kSrcCollection = 5,
+  // Item j of the read-major order is generated as in kSrcInitReadMajor and
+  // its first window gathered; the digit is (slice of the window's first 4
+  // bases, suffix length), slice * (L+1) + L - k, and each slice's rows go
+  // to that slice's own output arrays (split_vals / split_keys, rows counted
+  // from 0 there).  One pass lists every slice of a build that runs in
+  // several bucket slices.
+  kSrcInitSplit = 6,
+  // Item j of the read-major order over reads of any lengths (read i holds
+  // rows [off_i + i, off_i + i + L_i]) is generated and its first window
+  // gathered; the digit is the low byte of the suffix length.  Lists one
+  // slice (bucket filter) of a collection of mixed read lengths.
+  kSrcInitMixed = 7,
+  // Ids and the key window carried from the previous pass are loaded; the
+  // digit is byte key_shift / 8 of the suffix length (the high byte, after a
+  // kSrcInitMixed pass over reads longer than 255 bases).
+  kSrcCarriedLength = 8,
 };
 constexpr uint32_t kMaxPackCollections = 256;
+constexpr uint32_t kMaxSplit = 4;  // slices one kSrcInitSplit pass writes
 
 struct PassArgs {
   const void* vals_in;               // suffix ids (uint32 or uint64)
@@ -46,12 +63,17 @@ struct PassArgs {
   uint32_t key_shift;                // digit = (key >> key_shift) & 255
   uint32_t window_c0;                // gathered window: suffix bases [c0, c0 + 16)
   uint32_t n_reads;                  // generated modes
-  uint32_t bucket_shift;             // filter: keep rows with (key >> bucket_shift) in [bucket_lo, bucket_hi)
-  uint32_t bucket_lo, bucket_hi;
+  uint32_t key_lo, key_last;         // filter: keep rows whose first window w has w - key_lo <= key_last
   const uint32_t* coll_start;        // kSrcCollection: n_coll + 1 read starts
   uint32_t n_coll;
   uint32_t stall_tile0;              // test hook: tile 0 publishes nothing (its successor's wait runs out)
   uint64_t timeout_ns;               // look-back wait limit
+  // kSrcInitSplit: slice of every 4-base bucket (first window >> 24), and
+  // each slice's outputs and rows.
+  const uint8_t* split_of;
+  void* split_vals[kMaxSplit];
+  uint32_t* split_keys[kMaxSplit];
+  uint32_t split_rows[kMaxSplit];
 };
 
 // Tile geometry of the digit pass (threads x items per thread).
@@ -81,11 +103,21 @@ cudaError_t launch_identity(const ReadIndex& R, uint32_t n_reads, void* vals, in
 // zeroed uint64 counters).
 cudaError_t launch_bucket_hist(const ReadIndex& R, uint32_t n_reads, uint32_t bucket_bits, unsigned long long* hist,
                                int sm_count, cudaStream_t st);
-// First output row of each digit value, for the suffixes with bucket in
-// [lo, hi): row 0 = suffix length, rows 1..4 = first-window digits
-// (hist: 5 x 256 zeroed counters, replaced by exclusive sums).
-cudaError_t launch_pass_hist(const ReadIndex& R, uint32_t n_reads, uint32_t bucket_bits, uint32_t lo, uint32_t hi,
+// First output row of each digit value, for the suffixes whose first
+// window w has w - key_lo <= key_last: row 0 = low byte of the suffix
+// length, rows 1..4 = first-window digits, row 5 = high byte of the suffix
+// length (hist: 6 x 256 zeroed counters, replaced by exclusive sums).
+cudaError_t launch_pass_hist(const ReadIndex& R, uint32_t n_reads, uint32_t key_lo, uint32_t key_last,
                              uint32_t* hist, int sm_count, cudaStream_t st);
+// Suffixes whose first 8 bases (A-padded) are `prefix` (16 bits), counted by
+// their next 8 bases (hist: 65536 zeroed counters): the refinement of one
+// 8-base bucket by the characters that follow (Section 3.1).
+cudaError_t launch_sub_bucket_hist(const ReadIndex& R, uint32_t n_reads, uint32_t prefix, unsigned long long* hist,
+                                   int sm_count, cudaStream_t st);
+// First output row of each value of the four 8-bit digits of n keys (most
+// significant digit first): hist (4 x 256 zeroed counters) is replaced by
+// exclusive sums.
+cudaError_t launch_key_hist(const uint32_t* keys, uint64_t n, uint32_t* hist, int sm_count, cudaStream_t st);
 // min / max / sum of n lengths and the number of invalid ones (0 or > 65535):
 // out[0] = min, out[1] = max, out[2] = sum, out[3] = invalid (out zeroed by caller
 // except out[0] = UINT64_MAX).

@@ -65,8 +65,12 @@ template <class V, int THREADS, int IPT, int MIN_BLOCKS, int MODE, bool WRITE_KE
 __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs a) {
   constexpr int TILE = THREADS * IPT;
   constexpr int WARPS = THREADS / 32;
-  constexpr bool GEN = (MODE == kSrcInitUniform || MODE == kSrcInitReadMajor);
+  constexpr bool SPLIT = (MODE == kSrcInitSplit);  // digit = (slice, suffix length), per-slice outputs
+  constexpr bool MIXED = (MODE == kSrcInitMixed);  // read-major over reads of any lengths
+  constexpr bool GEN = (MODE == kSrcInitUniform || MODE == kSrcInitReadMajor || SPLIT || MIXED);
+  constexpr bool CARRY_KEY = (MODE == kSrcCarried || MODE == kSrcCarriedLength);
   constexpr bool LEN_DIGIT = (MODE == kSrcInitReadMajor);  // digit = suffix length, key = window 0
+  constexpr bool READ_MAJOR = (MODE == kSrcInitReadMajor || SPLIT);
   using I = typename std::conditional<GEN, uint64_t, uint32_t>::type;  // generated inputs may exceed 2^32 rows
   static_assert(THREADS >= 256 && THREADS % 32 == 0, "one thread per digit value is needed");
   static_assert(!FILTER || GEN, "the bucket filter applies to generated inputs");
@@ -82,6 +86,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
   __shared__ uint32_t s_scan[8];
   __shared__ uint32_t s_tile, s_kept;
   __shared__ uint32_t s_coll[MODE == kSrcCollection ? kMaxPackCollections + 1 : 1];
+  __shared__ uint8_t s_split[SPLIT ? kRadix : 1];  // slice of each 4-base bucket
 
   const V* vals_in = static_cast<const V*>(a.vals_in);
   V* vals_out = static_cast<V*>(a.vals_out);
@@ -90,6 +95,8 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
   for (int i = tid; i < kRadix; i += THREADS) s_thist[i] = 0u;
   if (MODE == kSrcCollection)
     for (uint32_t i = tid; i <= a.n_coll; i += THREADS) s_coll[i] = a.coll_start[i];
+  if (SPLIT)
+    for (int i = tid; i < kRadix; i += THREADS) s_split[i] = a.split_of[i];
   if (tid == 0) {
     const uint32_t t = atomicAdd(a.tile_counter, 1u);
     // Every id has been handed out once the last one is: reset for the next pass.
@@ -128,7 +135,40 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
           slen = min(slen + 1, L + 1);
         }
       }
-    } else if (MODE == kSrcInitReadMajor) {
+    } else if (MIXED) {
+      // Row idx of the read-major order over reads of any lengths: lane 0
+      // finds the read holding the warp's first row (a binary search over
+      // the read starts off_i + i), every lane steps to its own rows.
+      uint32_t i = 0;
+      if (lane == 0) {
+        uint32_t lo = 0, hi = a.n_reads;
+        while (hi - lo > 1) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if ((__ldg(a.R.desc + mid) >> 16) + mid <= warp_base - lane) lo = mid; else hi = mid;
+        }
+        i = lo;
+      }
+      i = __shfl_sync(0xFFFFFFFFu, i, 0);
+      uint64_t d = __ldg(a.R.desc + i);
+      uint32_t len = uint32_t(d & 0xFFFFu);
+      uint64_t k64 = uint64_t(warp_base) - ((d >> 16) + i);
+      while (k64 > len && i + 1 < a.n_reads) {
+        k64 -= len + 1;
+        d = __ldg(a.R.desc + ++i);
+        len = uint32_t(d & 0xFFFFu);
+      }
+      uint32_t k = uint32_t(k64);
+  #pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        val[j] = (V(i) << a.R.shift) | (V(k) << a.R.sym_bits);
+        k += 32;
+        while (k > len && i + 1 < a.n_reads) {  // rows past the last read are dropped below
+          k -= len + 1;
+          d = __ldg(a.R.desc + ++i);
+          len = uint32_t(d & 0xFFFFu);
+        }
+      }
+    } else if (READ_MAJOR) {
       // Row idx of the read-major order: read idx / (L+1), offset idx % (L+1),
       // stepped the same way.
       const uint32_t L1 = a.R.uniform_len + 1;
@@ -151,7 +191,7 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
         val[j] = (!NINTH || idx < n_in) ? __ldg(vals_in + idx) : V(0);
       }
     }
-    if (MODE == kSrcCarried) {
+    if (CARRY_KEY) {
   #pragma unroll
       for (int j = 0; j < IPT; ++j) {
         const I idx = warp_base + j * 32;
@@ -205,9 +245,15 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
     for (int j = 0; j < IPT; ++j) {
       const I idx = warp_base + j * 32;
       bool keep = !NINTH || idx < n_in;
-      if (FILTER) keep = keep && ((key[j] >> a.bucket_shift) - a.bucket_lo) < (a.bucket_hi - a.bucket_lo);
+      if (FILTER) keep = keep && (key[j] - a.key_lo) <= a.key_last;
       uint32_t d;
       if (LEN_DIGIT) d = a.R.uniform_len - ((uint32_t(val[j]) & ((1u << a.R.shift) - 1u)) >> a.R.sym_bits);
+      else if (MIXED || MODE == kSrcCarriedLength) {
+        const Suffix sx = decode(a.R, val[j]);
+        d = ((sx.len - sx.k) >> (MIXED ? 0u : a.key_shift)) & (kRadix - 1);
+      } else if (SPLIT)
+        d = uint32_t(s_split[key[j] >> 24]) * (a.R.uniform_len + 1u) + a.R.uniform_len -
+            ((uint32_t(val[j]) & ((1u << a.R.shift) - 1u)) >> a.R.sym_bits);
       else d = (key[j] >> a.key_shift) & (kRadix - 1);
       // Rows past the end (or filtered out) get a value no digit has, so they
       // match only each other and are neither counted nor written.
@@ -336,14 +382,31 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
       if (!NINTH || r < n_valid) {
         const uint32_t k = s_keys[r];
         const V v = s_vals[r];
+        const uint32_t kpos = (uint32_t(v) & ((1u << a.R.shift) - 1u)) >> a.R.sym_bits;
         uint32_t d;
-        if (LEN_DIGIT) d = a.R.uniform_len - ((uint32_t(v) & ((1u << a.R.shift) - 1u)) >> a.R.sym_bits);
+        if (LEN_DIGIT) d = a.R.uniform_len - kpos;
+        else if (MIXED || MODE == kSrcCarriedLength) {
+          const Suffix sx = decode(a.R, v);
+          d = ((sx.len - sx.k) >> (MIXED ? 0u : a.key_shift)) & (kRadix - 1);
+        }
+        else if (SPLIT) d = uint32_t(s_split[k >> 24]) * (a.R.uniform_len + 1u) + a.R.uniform_len - kpos;
         else d = (k >> a.key_shift) & (kRadix - 1);
         const uint32_t g = s_gbase[d] + r;
-        const bool ok = g < a.n_out;
-        if (ok) vals_out[g] = v;
-        if (WRITE_KEY && ok) a.keys_out[g] = k;
-        bad = bad || !ok;
+        if (SPLIT) {
+          // Rows of slice sl go to its own arrays, counted from 0 there.
+          const uint32_t sl = s_split[k >> 24];
+          const bool ok = sl < kMaxSplit && g < a.split_rows[sl < kMaxSplit ? sl : 0];
+          if (ok) {
+            static_cast<V*>(a.split_vals[sl])[g] = v;
+            a.split_keys[sl][g] = k;
+          }
+          bad = bad || !ok;
+        } else {
+          const bool ok = g < a.n_out;
+          if (ok) vals_out[g] = v;
+          if (WRITE_KEY && ok) a.keys_out[g] = k;
+          bad = bad || !ok;
+        }
       }
     }
     // Digit bases that disagree with the items: nothing was written out of bounds.
@@ -360,7 +423,11 @@ struct Shape {
   static constexpr int threads = T, ipt = I, min_blocks = B;
 };
 using ShapeMid = Shape<256, 16, 4>;    // 4096 items
-using ShapeLarge = Shape<512, 16, 2>;  // 8192 items
+using ShapeLarge = Shape<512, 16, 2>;  // 8192 items (32-bit ids)
+using Shape64x16 = Shape<256, 16, 3>;  // 4096 items, 64-bit ids: 48 KB staged holds an SM to three CTAs,
+                                       // so the registers are sized for three (no spills)
+using Shape64x12 = Shape<256, 12, 4>;  // 3072 items (64-bit ids: 36 KB staged, four CTAs per SM)
+using Shape64x8 = Shape<256, 8, 5>;    // 2048 items (64-bit ids: 24 KB staged, five CTAs per SM)
 
 template <class V, class S, int MODE, bool WK, bool F>
 cudaError_t launch_mode(const PassArgs& a, cudaStream_t st) {
@@ -408,6 +475,16 @@ cudaError_t launch_shape(const PassArgs& a, int mode, bool wk, bool filter, cuda
     case kSrcCollection:
       if (filter || wk) return cudaErrorInvalidValue;
       return launch_mode<V, S, kSrcCollection, false, false>(a, st);
+    case kSrcInitSplit:
+      if (filter || !wk) return cudaErrorInvalidValue;  // it writes every slice's ids and keys
+      return launch_mode<V, S, kSrcInitSplit, true, false>(a, st);
+    case kSrcInitMixed:
+      if (!wk) return cudaErrorInvalidValue;  // it exists to list window 0
+      return filter ? launch_mode<V, S, kSrcInitMixed, true, true>(a, st)
+                    : launch_mode<V, S, kSrcInitMixed, true, false>(a, st);
+    case kSrcCarriedLength:
+      if (filter || !wk) return cudaErrorInvalidValue;
+      return launch_mode<V, S, kSrcCarriedLength, true, false>(a, st);
     default: return cudaErrorInvalidValue;
   }
 }

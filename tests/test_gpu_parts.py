@@ -115,7 +115,7 @@ def test_rounds_resume_on_gpu(ctx, tmp_path):  # noqa: F811
     assert st["counts"] == [int(x) for x in ref["counts"]]
 
 
-def test_part_rejects_bad_ranges_and_mixed_lengths(ctx):  # noqa: F811
+def test_part_rejects_bad_ranges(ctx):  # noqa: F811
     from paper_1401_7457_gb300 import binding
     codes, lens = _collection(100, 50, 59)
     words = binding.pack_codes(codes)
@@ -123,10 +123,24 @@ def test_part_rejects_bad_ranges_and_mixed_lengths(ctx):  # noqa: F811
         with pytest.raises(binding.CxbwtError) as e:
             ctx.build_part(words, lens, lo, hi, 0, 10)
         assert e.value.status == -1
-    codes2, lens2 = synth.mixed_length_reads(50, 20, 60, 3)
-    with pytest.raises(binding.CxbwtError) as e:
-        ctx.bucket_counts(binding.pack_codes(codes2), lens2)
-    assert e.value.status == -5
+
+
+@pytest.mark.parametrize("n_parts", [1, 3])
+def test_parts_of_mixed_read_lengths(ctx, n_parts):  # noqa: F811
+    """Reads of 20 to 300 bases: the bucket counts sum to N, and the parts
+    (each listed with the mixed-length generated pass and, past 255 bases,
+    the high byte of the suffix length) merge to the oracle's result."""
+    from paper_1401_7457_gb300 import binding, parts
+    codes, lens = synth.mixed_length_reads(6000, 20, 300, 3)
+    ref = oracle_of(codes, lens)
+    words = binding.pack_codes(codes)
+    counts = ctx.bucket_counts(words, lens)
+    assert int(counts.sum()) == len(ref["bwt"])
+    res = parts.empty_result(len(ref["bwt"]), lens.size)
+    for p in parts.plan_parts(counts, n_parts):
+        parts.merge_into(res, p, *parts.build_part_host(ctx, words, lens, p, bucket_counts=counts))
+    assert np.array_equal(res[0], _words(ref["bwt"]))
+    assert np.array_equal(res[1], ref["dollar_pos"])
 
 
 def test_part_rejects_counts_of_another_collection(ctx):  # noqa: F811

@@ -54,6 +54,45 @@ def test_slices_identical(genome_reads, slices, flags, where):
         assert st["slices"] >= 2, st
 
 
+def split_budget(n_suffixes, id_bytes=4, host=False):
+    """A budget under which the build needs two slices but holds ids and keys
+    for all N rows plus one spare slice: the single listing pass of every
+    slice (digit = slice, suffix length) is then taken.  Rows cost
+    2 * (id + key) bytes per row of the largest slice when each slice lists
+    its own suffixes, and (id + key) bytes per row of N plus of the largest
+    slice with the single pass; the budget sits halfway between."""
+    fixed = (2 << 20) + 0.5 * n_suffixes  # tables, look-back words
+    if host:
+        fixed += (8 << 20) + 0.6 * n_suffixes  # read store and output staging
+    one_per_row = 2 * id_bytes + 8 + 8 / 33 + (8 if host else 0)  # host: the suffix order's staging
+    split_per_n = 1.53 * (id_bytes + 4) + 0.53 * (8 / 33 + 8 / 1025) + (0.53 * 8 if host else 0)
+    return int(fixed + n_suffixes * (one_per_row + split_per_n) / 2)
+
+
+@pytest.mark.parametrize("flags", [0, 1, 8, 9])
+@pytest.mark.parametrize("where", ["device", "host"])
+def test_split_listing_pass(genome_reads, flags, where):
+    """Two slices listed by one generating pass over every suffix (each
+    slice's rows written to its own part of one array, ordered by suffix
+    length, then sorted between that part and a spare array): the oracle's
+    result, suffix order included, with 32- and 64-bit ids, with and without
+    the preceding base in the ids."""
+    _need_gpu()
+    from paper_1401_7457_gb300 import binding
+    codes, lens, ref = genome_reads
+    N = int(lens.sum()) + lens.size
+    idb = 8 if flags & 1 else 4
+    with binding.Context(device=0, budget_bytes=split_budget(N, idb, where == "host"), plan_flags=flags) as c:
+        got = gpu_bwt(c, codes, lens, where=where, want_sa=True)
+        st = c.stats()
+    assert_same(got, ref, sa=True)
+    assert st["slices"] == 2, st
+    # One listing pass, then the four window passes of each slice (a pass per
+    # slice listing its suffixes would make ten).
+    assert st["sort_pass_launches"] == 9, st
+    assert st["carried_pass_launches"] == 8, st
+
+
 def test_uniform_random_slices():
     """i.i.d. reads (mostly distinct 16-base prefixes) in several slices."""
     _need_gpu()
@@ -85,8 +124,31 @@ def test_slices_from_8_base_buckets():
         assert c.stats()["slices"] >= 11
 
 
+def test_refined_8_base_bucket():
+    """Reads of 20 bases that all start with AAAAAAAA, under a budget of
+    about 14 slices: the 8-base bucket AAAAAAAA holds the n terminator-only
+    suffixes and the n whole reads (2/21 of all suffixes), more than a slice
+    can hold, so it is refined by the next 8 bases (Section 3.1) into 16-base
+    buckets, the largest of which holds the n terminators (1/21)."""
+    _need_gpu()
+    from paper_1401_7457_gb300 import binding
+    codes, lens = synth.uniform_reads(600_000, 20, 65)
+    codes = codes.reshape(-1, 20).copy()
+    codes[:, :8] = 0
+    codes = codes.ravel()
+    ref = oracle_of(codes, lens)
+    N = int(lens.sum()) + lens.size
+    for where in ("device", "host"):
+        # Host buffers also hold the read store and the output staging on the device.
+        budget = budget_for(N, 14, host_sa=where == "host") + (20 << 20 if where == "host" else 0)
+        with binding.Context(device=0, budget_bytes=budget) as c:
+            assert_same(gpu_bwt(c, codes, lens, where=where, want_sa=True), ref, sa=True)
+            assert c.stats()["slices"] >= 11
+
+
 def test_one_bucket_larger_than_a_slice_is_enomem():
-    """All-A reads put every suffix in one 8-base bucket: no slice can hold it."""
+    """All-A reads put every suffix in one 16-base bucket, even after the
+    refinement of the 8-base bucket: no slice can hold it."""
     _need_gpu()
     from paper_1401_7457_gb300 import binding
     codes, lens = np.zeros(20_000 * 50, dtype=np.uint8), np.full(20_000, 50, dtype=np.uint32)
@@ -97,14 +159,19 @@ def test_one_bucket_larger_than_a_slice_is_enomem():
         assert e.value.status == -2
 
 
-def test_mixed_lengths_need_one_slice():
+@pytest.mark.parametrize("lo,hi", [(50, 100), (1, 30), (200, 300)])
+@pytest.mark.parametrize("flags", [0, 1])
+def test_mixed_length_slices(lo, hi, flags):
+    """Reads of mixed lengths in several slices: each slice lists its
+    suffixes in read-major order over reads of any length (a binary search
+    for each warp's first read), ordered by the low then, past 255 bases, the
+    high byte of the suffix length; with 32- and 64-bit ids."""
     _need_gpu()
     from paper_1401_7457_gb300 import binding
-    codes, lens = synth.mixed_length_reads(20_000, 50, 100, 64)
+    n = {30: 200_000, 100: 20_000, 300: 6_000}[hi]  # a few million suffixes: several slices under the budget
+    codes, lens = synth.mixed_length_reads(n, lo, hi, 64)
+    ref = oracle_of(codes, lens)
     N = int(lens.sum()) + lens.size
-    with binding.Context(device=0, budget_bytes=budget_for(N, 4)) as c:
-        with pytest.raises(binding.CxbwtError) as e:
-            c.build(binding.pack_codes(codes), lens)
-        assert e.value.status == -5
-    with binding.Context(device=0, plan_flags=1) as c:  # 64-bit ids, one slice
-        assert_same(gpu_bwt(c, codes, lens, want_sa=True), oracle_of(codes, lens), sa=True)
+    with binding.Context(device=0, budget_bytes=budget_for(N, 4, 8 if flags else 4), plan_flags=flags) as c:
+        assert_same(gpu_bwt(c, codes, lens, want_sa=True), ref, sa=True)
+        assert c.stats()["slices"] >= 3
