@@ -39,7 +39,9 @@ struct SegArgs {
 // Key words a group remainder is sorted by for reads of at most max_len bases
 // (a compiled width >= ceil((max_len - 16) / 16)), or 0 if too long.
 int segsort_words(uint32_t max_len);
-cudaError_t launch_segsort(const SegArgs& a, int nw, int id_bytes, int sm_count, cudaStream_t st);
+// wide: warp windows of 64 rows (two per lane) instead of 32, for read
+// stores out of L2.
+cudaError_t launch_segsort(const SegArgs& a, int nw, int id_bytes, int sm_count, bool wide, cudaStream_t st);
 // Digit bases (exclusive, per digit position) of windows 1 .. n_win over n rows of vals.
 cudaError_t launch_range_hist(const void* vals, int id_bytes, uint32_t n, const ReadIndex& R, uint32_t n_win,
                               uint32_t* hist, int sm_count, cudaStream_t st);

@@ -14,15 +14,17 @@
 //     with A's, and then the shorter one is smaller - the group is already in
 //     (length, read) order, so they form its prefix and stay where they are;
 //   * the rest of the group (the "remainder") is sorted by bases 16.. of the
-//     suffix, A-padded, ties kept in the current order (stable): one warp
-//     with a register bitonic network when it has at most 32 members, one CTA
-//     with a shared-memory bitonic network up to kCtaMax members, and larger
-//     ones are listed for the host, which finishes them with more LSD passes
+//     suffix, A-padded, ties kept in the current order (stable): by one warp
+//     when it has at most 64 members (32 for the widest keys) - each member
+//     counts the members that order before it -, by one CTA with a
+//     shared-memory bitonic network up to kCtaMax members, and larger ones
+//     are listed for the host, which finishes them with more LSD passes
 //     restricted to their rows (k_range_hist gives those passes' digit bases).
 //
 // Each warp walks the groups that start in its chunk of rows in windows of
-// at most 32 rows made of whole groups, and sorts a window with one segmented
-// register network, so no group list is materialised for the common case.
+// at most 64 rows made of whole groups (two rows per lane), and ranks a
+// window's rows against their groups in per-warp shared memory, so no group
+// list is materialised for the common case.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -135,63 +137,115 @@ __device__ __forceinline__ uint32_t suffix_len(const ReadIndex& R, V v) {
   return s.len - s.k;
 }
 
-// Finish the groups of a window of up to 32 rows (lane l holds row cur + l):
-// rows [gid, gend) of the window form the lane's group.  Each row counts the
-// members of its group that order before it - smaller bases 16.. (A-padded),
-// or equal bases and an earlier row (stable) - and moves to gid + that count.
-// Rows of at most 16 bases gather all-zero words, so they keep their place at
-// the front of their group; `need` is false for rows alone in their group.
-template <int NW>
+// Finish the groups of a window of up to SPAN rows (SPAN = 32 or 64) made
+// of whole groups: lane l holds rows l, l + 32, ... (ROUNDS = SPAN / 32 of
+// them).  Each row counts the members of its group that order before it -
+// smaller bases 16.. (A-padded), or equal bases and an earlier row (stable) -
+// and moves to its group's first row + that count.  Rows of at most 16 bases
+// gather all-zero words, so they keep their place at the front of their
+// group; a row alone in its group neither gathers nor moves.  heads bit r
+// says that row r of the window starts a group (bit 0 is always set).
+//
+// The ranking runs in ROUNDS rounds of 32 rows, each as long as the largest
+// group among its rows: a window of several groups of 20 or so rows (reads
+// at tens-fold coverage) keeps most lanes busy, where windows of 32 rows
+// would hold one such group each.
+template <int NW, int SPAN>
 struct RowWords {
   static constexpr int kStride = (NW + 3) / 4 * 4;  // words per row, a whole number of uint4
-  uint4 r[32][kStride / 4];
+  uint4 r[SPAN][kStride / 4];
 };
 
-template <int NW, class V>
-__device__ void warp_rank_window(const SegArgs& a, uint32_t cur, uint32_t n_rows, uint32_t gid, uint32_t gend,
-                                 bool need, int lane, RowWords<NW>& sw) {
-  constexpr int Q = RowWords<NW>::kStride / 4;
+template <int SPAN>
+struct Heads;
+template <>
+struct Heads<32> {
+  using T = uint32_t;
+};
+template <>
+struct Heads<64> {
+  using T = unsigned long long;
+};
+
+template <int NW, int SPAN, class V>
+__device__ void warp_rank_window(const SegArgs& a, uint32_t cur, uint32_t n_rows, typename Heads<SPAN>::T heads,
+                                 int lane, RowWords<NW, SPAN>& sw) {
+  using H = typename Heads<SPAN>::T;
+  constexpr int ROUNDS = SPAN / 32;
+  constexpr int Q = RowWords<NW, SPAN>::kStride / 4;
   V* vals = static_cast<V*>(a.vals);
-  const bool live = uint32_t(lane) < n_rows;
-  uint32_t w[Q * 4];
-  V v = 0;
+  V v[ROUNDS];
+  uint32_t gid[ROUNDS], gsize[ROUNDS];
 #pragma unroll
-  for (int i = 0; i < Q * 4; ++i) w[i] = 0u;
-  if (live) {
-    v = vals[cur + lane];
-    if (need) {
-      uint32_t g[NW];
-      gather_words<NW>(a.R, decode(a.R, v), a.depth, g);
+  for (int h = 0; h < ROUNDS; ++h) {
+    const uint32_t row = uint32_t(lane) + 32u * h;
+    const bool live = row < n_rows;
+    // The row's group: from the last head at or before it to the next head after it.
+    const H upto = heads & (row + 1 >= uint32_t(SPAN) ? ~H(0) : ((H(2) << row) - 1));
+    const uint32_t g0 = uint32_t(8 * sizeof(H) - 1) - (sizeof(H) == 8 ? __clzll((long long)upto) : __clz(uint32_t(upto)));
+    const H after = heads & ~upto;
+    const uint32_t ge = after ? min(uint32_t(sizeof(H) == 8 ? __ffsll((long long)after) : __ffs(uint32_t(after))) - 1,
+                                    n_rows)
+                              : n_rows;
+    gid[h] = g0;
+    gsize[h] = live ? ge - g0 : 0u;
+    uint32_t w[Q * 4];
 #pragma unroll
-      for (int i = 0; i < NW; ++i) w[i] = g[i];
+    for (int i = 0; i < Q * 4; ++i) w[i] = 0u;
+    v[h] = 0;
+    if (live) {
+      v[h] = vals[cur + row];
+      if (gsize[h] > 1) {
+        uint32_t g[NW];
+        gather_words<NW>(a.R, decode(a.R, v[h]), a.depth, g);
+#pragma unroll
+        for (int i = 0; i < NW; ++i) w[i] = g[i];
+      }
     }
+    // Publish this row's words for the other members of its group.
+#pragma unroll
+    for (int q = 0; q < Q; ++q) sw.r[row][q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
   }
-  // Publish this row's words for the other members of its group.
-#pragma unroll
-  for (int q = 0; q < Q; ++q) sw.r[lane][q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
   __syncwarp();
-  const uint32_t gsize = live ? gend - gid : 0u;
-  uint32_t rank = 0;
-  uint32_t mine[NW];
+  uint32_t rank[ROUNDS];
 #pragma unroll
-  for (int i = 0; i < NW; ++i) mine[i] = w[i];
-  for (uint32_t t = 0; t < gsize; ++t) {
-    const uint32_t src = gid + t;
-    // Row src orders before this row: smaller words, or equal words and an
-    // earlier row.  Lanes of one group read one row: a broadcast.
-    uint32_t ov[NW];
+  for (int h = 0; h < ROUNDS; ++h) {
+    const uint32_t row = uint32_t(lane) + 32u * h;
+    uint32_t mine[NW];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      const uint4 o = sw.r[src][q];
-      if (4 * q < NW) ov[4 * q] = o.x;
-      if (4 * q + 1 < NW) ov[4 * q + 1] = o.y;
-      if (4 * q + 2 < NW) ov[4 * q + 2] = o.z;
-      if (4 * q + 3 < NW) ov[4 * q + 3] = o.w;
+      const uint4 o = sw.r[row][q];
+      if (4 * q < NW) mine[4 * q] = o.x;
+      if (4 * q + 1 < NW) mine[4 * q + 1] = o.y;
+      if (4 * q + 2 < NW) mine[4 * q + 2] = o.z;
+      if (4 * q + 3 < NW) mine[4 * q + 3] = o.w;
     }
-    rank -= lex_less_mask<NW>(ov, src, mine, uint32_t(lane));  // ~0u is -1
+    uint32_t rk = 0;
+    const uint32_t n_cmp = gsize[h] > 1 ? gsize[h] : 0u;
+    for (uint32_t t = 0; t < n_cmp; ++t) {
+      const uint32_t src = gid[h] + t;
+      // Row src orders before this row: smaller words, or equal words and an
+      // earlier row.  Lanes of one group read one row: a broadcast.
+      uint32_t ov[NW];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const uint4 o = sw.r[src][q];
+        if (4 * q < NW) ov[4 * q] = o.x;
+        if (4 * q + 1 < NW) ov[4 * q + 1] = o.y;
+        if (4 * q + 2 < NW) ov[4 * q + 2] = o.z;
+        if (4 * q + 3 < NW) ov[4 * q + 3] = o.w;
+      }
+      rk -= lex_less_mask<NW>(ov, src, mine, row);  // ~0u is -1
+    }
+    rank[h] = rk;
   }
-  __syncwarp();  // every lane has read its row and the shared words before any overwrite
-  if (live && gid + rank != uint32_t(lane)) vals[cur + gid + rank] = v;
+  __syncwarp();  // every lane has read its rows and the shared words before any write
+#pragma unroll
+  for (int h = 0; h < ROUNDS; ++h) {
+    const uint32_t row = uint32_t(lane) + 32u * h;
+    if (gsize[h] > 1 && gid[h] + rank[h] != row) vals[cur + gid[h] + rank[h]] = v[h];
+  }
+  __syncwarp();  // the next window reuses the shared rows
 }
 
 // First row r >= from (r < n) whose window differs from row r-1, or n.
@@ -215,10 +269,10 @@ __device__ uint32_t next_head(const SegArgs& a, uint32_t from, int lane) {
   }
 }
 
-// Finish one group of more than 32 rows [gs, ge): skip its finished prefix,
-// sort a remainder of at most 32 rows here, list a larger one.
-template <int NW, class V>
-__device__ void finish_long_group(const SegArgs& a, uint32_t gs, uint32_t ge, int lane, RowWords<NW>& sw) {
+// Finish one group of more than SPAN rows [gs, ge): skip its finished
+// prefix, sort a remainder of at most SPAN rows here, list a larger one.
+template <int NW, int SPAN, class V>
+__device__ void finish_long_group(const SegArgs& a, uint32_t gs, uint32_t ge, int lane, RowWords<NW, SPAN>& sw) {
   const V* vals = static_cast<const V*>(a.vals);
   uint32_t lo = gs, hi = ge;
   while (lo < hi) {
@@ -227,8 +281,8 @@ __device__ void finish_long_group(const SegArgs& a, uint32_t gs, uint32_t ge, in
   }
   const uint32_t m = ge - lo;
   if (m < 2) return;
-  if (m <= 32) {
-    warp_rank_window<NW, V>(a, lo, m, 0u, m, true, lane, sw);
+  if (m <= uint32_t(SPAN)) {
+    warp_rank_window<NW, SPAN, V>(a, lo, m, typename Heads<SPAN>::T(1), lane, sw);
   } else if (lane == 0) {
     // Up to kSmallCta rows: cta_list from the front (counts[0]); up to
     // CtaRows: cta_list from the back (counts[3]; the two never meet, as each
@@ -247,46 +301,49 @@ __device__ void finish_long_group(const SegArgs& a, uint32_t gs, uint32_t ge, in
 }
 
 // Each warp owns the groups whose first row lies in its chunk of kChunk rows
-// and walks them in windows of up to 32 rows made of whole groups.
-template <int NW, class V>
+// and walks them in windows of up to SPAN rows made of whole groups.  SPAN is
+// 64 (two rows per lane) when the read store is out of L2: the gathers of a
+// window then wait on DRAM, and a window of two rows per lane puts twice as
+// many in flight and spends fewer rounds on groups of 20 to 30 rows (reads at
+// tens-fold coverage); with the store in L2 the ranking's instructions
+// dominate and 32-row windows, with fewer of them, are faster (measured).
+template <int NW, class V, int SPAN>
 __global__ void __launch_bounds__(256) k_segsort_warp(const SegArgs a) {
+  using H = typename Heads<SPAN>::T;
   const int lane = threadIdx.x & 31;
-  __shared__ RowWords<NW> s_rows[8];
-  RowWords<NW>& sw = s_rows[threadIdx.x >> 5];
+  __shared__ RowWords<NW, SPAN> s_rows[8];
+  RowWords<NW, SPAN>& sw = s_rows[threadIdx.x >> 5];
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t n_chunks = (a.n_items + kChunk - 1) / kChunk;
   for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_chunks; c += warps) {
     const uint32_t limit = min((c + 1) * kChunk, a.n_items);
     uint32_t cur = next_head(a, c * kChunk, lane);
     while (cur < limit) {
-      // Heads among rows cur+1 .. cur+32 (bit l-1 for row cur+l); row limit
-      // and beyond belong to the next chunk's groups, so the first head at or
-      // after limit ends this chunk's last group.
-      const uint32_t y = cur + 1 + lane;
-      bool head = (y >= a.n_items) || (a.keys[y] != a.keys[y - 1]);
-      uint32_t hm = __ballot_sync(0xFFFFFFFFu, head);
-      // Drop heads after the first one at or past limit.
-      const uint32_t past = __ballot_sync(0xFFFFFFFFu, head && y >= limit);
+      // Heads among rows cur+1 .. cur+SPAN (bit r-1 for row cur+r); row
+      // limit and beyond belong to the next chunk's groups, so the first
+      // head at or after limit ends this chunk's last group.
+      H hm = 0, past = 0;
+#pragma unroll
+      for (int h = 0; h < SPAN / 32; ++h) {
+        const uint32_t y = cur + 1 + lane + 32u * h;
+        const bool head = (y >= a.n_items) || (a.keys[y] != a.keys[y - 1]);
+        hm |= H(__ballot_sync(0xFFFFFFFFu, head)) << (32 * h);
+        past |= H(__ballot_sync(0xFFFFFFFFu, head && y >= limit)) << (32 * h);
+      }
       if (past) hm &= (past & (~past + 1)) * 2u - 1u;  // keep bits up to the lowest one in past
-      if (hm == 0) {  // the group at cur has more than 32 rows
-        const uint32_t ge = next_head(a, cur + 33, lane);
-        finish_long_group<NW, V>(a, cur, ge, lane, sw);
+      if (hm == 0) {  // the group at cur has more than SPAN rows
+        const uint32_t ge = next_head(a, cur + SPAN + 1, lane);
+        finish_long_group<NW, SPAN, V>(a, cur, ge, lane, sw);
         cur = ge;
         continue;
       }
-      const uint32_t n_rows = 32u - __clz(hm);  // rows up to the last usable head
-      // heads_at bit l: row cur+l starts a group (row cur does).
-      const uint32_t heads_at = (hm << 1) | 1u;
+      // Rows up to the last usable head; heads bit r: row cur+r starts a group.
+      const uint32_t n_rows =
+          uint32_t(SPAN) - (sizeof(H) == 8 ? __clzll((long long)hm) : __clz(uint32_t(hm)));
+      const H heads = (hm << 1) | H(1);
       // A window of only one-row groups is already sorted.
-      const uint32_t full = n_rows == 32 ? 0xFFFFFFFFu : ((1u << n_rows) - 1u);
-      if ((heads_at & full) != full) {
-        // The lane's group: from the last head at or before it to the next head after it.
-        const uint32_t upto = heads_at & (lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u));
-        const uint32_t gid = 31u - __clz(upto);
-        const uint32_t after = lane == 31 ? 0u : (heads_at & ~((2u << lane) - 1u));
-        const uint32_t gend = after ? min(uint32_t(__ffs(after) - 1), n_rows) : n_rows;
-        warp_rank_window<NW, V>(a, cur, n_rows, gid, gend, gend - gid > 1, lane, sw);
-      }
+      const H full = n_rows == uint32_t(SPAN) ? ~H(0) : ((H(1) << n_rows) - 1);
+      if ((heads & full) != full) warp_rank_window<NW, SPAN, V>(a, cur, n_rows, heads, lane, sw);
       cur += n_rows;
     }
   }
@@ -429,13 +486,15 @@ cudaError_t launch_cta_nw(const SegArgs& a, uint32_t grid, const uint2* list, co
 // The warp kernel, then the small-group and the large-group CTA kernels over
 // the two ends of the list it fills.
 template <int NW, class V>
-cudaError_t launch_nw(const SegArgs& a, int sm_count, cudaStream_t st) {
+cudaError_t launch_nw(const SegArgs& a, int sm_count, bool wide, cudaStream_t st) {
   const uint32_t n_chunks = (a.n_items + kChunk - 1) / kChunk;
   uint32_t blocks = (n_chunks + 7) / 8;
   const uint32_t cap = uint32_t(sm_count) * 16;
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
-  k_segsort_warp<NW, V><<<blocks, 256, 0, st>>>(a);
+  // Rows of the widest keys (long reads) would not fit twice in shared memory.
+  if (wide && NW <= 16) k_segsort_warp<NW, V, (NW <= 16 ? 64 : 32)><<<blocks, 256, 0, st>>>(a);
+  else k_segsort_warp<NW, V, 32><<<blocks, 256, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = launch_cta_nw<NW, V, kSmallCta, 128>(a, uint32_t(sm_count) * 16, a.cta_list, a.counts + 0, a.cta_cap, 1,
@@ -446,17 +505,17 @@ cudaError_t launch_nw(const SegArgs& a, int sm_count, cudaStream_t st) {
 }
 
 template <class V>
-cudaError_t launch_v(const SegArgs& a, int nw, int sm_count, cudaStream_t st) {
+cudaError_t launch_v(const SegArgs& a, int nw, int sm_count, bool wide, cudaStream_t st) {
   switch (nw) {
-    case 2: return launch_nw<2, V>(a, sm_count, st);
-    case 4: return launch_nw<4, V>(a, sm_count, st);
-    case 6: return launch_nw<6, V>(a, sm_count, st);
-    case 8: return launch_nw<8, V>(a, sm_count, st);
-    case 10: return launch_nw<10, V>(a, sm_count, st);
-    case 12: return launch_nw<12, V>(a, sm_count, st);
-    case 16: return launch_nw<16, V>(a, sm_count, st);
-    case 24: return launch_nw<24, V>(a, sm_count, st);
-    case 32: return launch_nw<32, V>(a, sm_count, st);
+    case 2: return launch_nw<2, V>(a, sm_count, wide, st);
+    case 4: return launch_nw<4, V>(a, sm_count, wide, st);
+    case 6: return launch_nw<6, V>(a, sm_count, wide, st);
+    case 8: return launch_nw<8, V>(a, sm_count, wide, st);
+    case 10: return launch_nw<10, V>(a, sm_count, wide, st);
+    case 12: return launch_nw<12, V>(a, sm_count, wide, st);
+    case 16: return launch_nw<16, V>(a, sm_count, wide, st);
+    case 24: return launch_nw<24, V>(a, sm_count, wide, st);
+    case 32: return launch_nw<32, V>(a, sm_count, wide, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -478,8 +537,8 @@ int segsort_words(uint32_t max_len) {
   return 0;  // reads too long for the on-chip finish
 }
 
-cudaError_t launch_segsort(const SegArgs& a, int nw, int id_bytes, int sm_count, cudaStream_t st) {
-  return id_bytes == 8 ? launch_v<uint64_t>(a, nw, sm_count, st) : launch_v<uint32_t>(a, nw, sm_count, st);
+cudaError_t launch_segsort(const SegArgs& a, int nw, int id_bytes, int sm_count, bool wide, cudaStream_t st) {
+  return id_bytes == 8 ? launch_v<uint64_t>(a, nw, sm_count, wide, st) : launch_v<uint32_t>(a, nw, sm_count, wide, st);
 }
 
 cudaError_t launch_range_hist(const void* vals, int id_bytes, uint32_t n, const ReadIndex& R, uint32_t n_win,

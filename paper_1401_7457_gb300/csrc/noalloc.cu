@@ -203,7 +203,7 @@ extern "C" int cxbwt_build_noalloc(const uint32_t* reads_2bit, uint64_t n_reads,
     g.big_cap = uint32_t(kBigCap);
     g.counts = d_seg;
     g.err = d_err;
-    NA_CUDA(launch_segsort(g, seg_words, 4, sm_count, st));
+    NA_CUDA(launch_segsort(g, seg_words, 4, sm_count, false, st));
     uint32_t seg_counts[2] = {0, 0};
     NA_CUDA(cudaMemcpyAsync(seg_counts, d_seg, 8, cudaMemcpyDeviceToHost, st));
     NA_CUDA(cudaStreamSynchronize(st));
