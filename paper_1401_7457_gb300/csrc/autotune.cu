@@ -1,7 +1,8 @@
 // cxbwt_autotune: choose the tile shape and sort plan by timing them.
 //
 // For one collection (device memory), every candidate (tile of 4096 or 8192
-// items, group plan or LSD plan where both apply) is built twice and timed
+// items with 32-bit suffix ids, of 2048, 3072 or 4096 with 64-bit ones;
+// group plan or LSD plan where both apply) is built twice and timed
 // with CUDA events on the caller's stream; the fastest choice is kept in the
 // context for builds of the same maximum read length and size class (N
 // within a factor of two).  Builds whose options leave the tile and the plan
@@ -30,17 +31,26 @@ extern "C" int cxbwt_autotune(cxbwt_ctx* c, const uint32_t* reads_2bit, uint64_t
     h = hl.data();
   }
   uint64_t N = n_reads;
-  uint32_t Lmax = 0;
+  uint32_t Lmax = 0, Lmin = ~0u;
   for (uint64_t i = 0; i < n_reads; ++i) {
     N += h[i];
     Lmax = std::max(Lmax, h[i]);
+    Lmin = std::min(Lmin, h[i]);
   }
+  // The id width the build will use decides which tiles exist.
+  Plan probe;
+  probe.n = n_reads;
+  probe.Lmax = Lmax;
+  probe.uniform = Lmin == Lmax;
+  plan_ids(probe, (c->opt.plan_flags & CXBWT_PLAN_ID64) != 0, false);
   const cxbwt_options saved = c->opt;
   const auto saved_tuned = c->tuned;
   c->tuned.clear();
   struct Cand { int tile, algo; };
-  std::vector<Cand> cands = {{4096, CXBWT_ALGO_GROUPS}, {8192, CXBWT_ALGO_GROUPS}, {4096, CXBWT_ALGO_LSD},
-                             {8192, CXBWT_ALGO_LSD}};
+  std::vector<Cand> cands;
+  const std::vector<int> tiles = probe.idb == 8 ? std::vector<int>{2048, 3072, 4096} : std::vector<int>{4096, 8192};
+  for (int algo : {CXBWT_ALGO_GROUPS, CXBWT_ALGO_LSD})
+    for (int t : tiles) cands.push_back(Cand{t, algo});
   cudaEvent_t e0, e1;
   CX_CUDA(c, cudaEventCreate(&e0));
   CX_CUDA(c, cudaEventCreate(&e1));

@@ -7,6 +7,12 @@ namespace cxbwt {
 TileShape onesweep_shape(int tile_items_hint, int id_bytes) {
   if (id_bytes == 4 && tile_items_hint == 8192)
     return TileShape{onesweep::ShapeLarge::threads, onesweep::ShapeLarge::ipt};
+  if (id_bytes == 8 && tile_items_hint == 2048)
+    return TileShape{onesweep::Shape64x8::threads, onesweep::Shape64x8::ipt};
+  if (id_bytes == 8 && tile_items_hint == 3072)
+    return TileShape{onesweep::Shape64x12::threads, onesweep::Shape64x12::ipt};
+  // Everything else: 4096-item tiles (for 64-bit ids the instantiation whose
+  // registers are sized for the three CTAs its shared memory allows).
   return TileShape{onesweep::ShapeMid::threads, onesweep::ShapeMid::ipt};
 }
 
