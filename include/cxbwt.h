@@ -80,7 +80,8 @@ typedef struct {
                                    any other value gives CXBWT_EUNSUPPORTED */
   int digit_bits;               /* radix digit width; 8 is the only width built (0 = 8, others give
                                    CXBWT_EUNSUPPORTED) */
-  int tile_items;               /* items per radix tile; 0 = automatic */
+  int tile_items;               /* items per radix tile: 0 = automatic (4096); 4096 or 8192 with 32-bit
+                                   suffix ids, 2048, 3072 or 4096 with 64-bit ones */
   int async;                    /* nonzero: calls return after enqueue when outputs are on the device */
   int timing;                   /* nonzero: record CUDA events around every phase (see cxbwt_stats) */
   int algorithm;                /* CXBWT_ALGO_*: how the suffixes are sorted (all give identical output) */
@@ -207,14 +208,14 @@ int cxbwt_build_sa(cxbwt_ctx* ctx, const uint32_t* reads_2bit, uint64_t n_reads,
  * (rounds).  B_R is the concatenation of the ranges' parts in bucket order,
  * because every suffix of a lower bucket sorts before every suffix of a
  * higher one.  Here a bucket is the first 8 bases of a suffix, A-padded past
- * the read end (CXBWT_BUCKETS of them).  Parts need reads of one length (at
- * most 528 bases).  The 8-base buckets are never split: a part holds whole
- * buckets. */
+ * the read end (CXBWT_BUCKETS of them).  Parts need reads of at most 528
+ * bases (of one length or not).  A part holds whole 8-base buckets (inside a
+ * part, a bucket larger than a device-memory slice is split by its next 8
+ * bases). */
 #define CXBWT_BUCKETS 65536u
 
 /* Suffixes per bucket (Figure 2 step 1): out_counts (host, CXBWT_BUCKETS
- * entries) receives the counts; they sum to N.  Synchronous.  EUNSUPPORTED
- * for reads of mixed lengths. */
+ * entries) receives the counts; they sum to N.  Synchronous. */
 int cxbwt_bucket_counts(cxbwt_ctx* ctx, const uint32_t* reads_2bit, uint64_t n_reads, const uint32_t* lens,
                         uint64_t* out_counts, void* stream);
 
@@ -245,7 +246,7 @@ int cxbwt_split_parts(const uint64_t* counts, uint32_t n_buckets, uint32_t n_par
  *   out_counts      5 entries (may be NULL): the part's symbol counts (they
  *                   add up over the parts)
  * The caller owns every buffer.  Returns as cxbwt_build; EINVAL for a bad
- * bucket range, EUNSUPPORTED for mixed read lengths. */
+ * bucket range. */
 int cxbwt_build_part(cxbwt_ctx* ctx, const uint32_t* reads_2bit, uint64_t n_reads, const uint32_t* lens,
                      uint32_t bucket_lo, uint32_t bucket_hi, const uint64_t* bucket_counts, uint32_t* out_words,
                      uint64_t* out_dollar_pos, uint64_t* out_counts, uint64_t* out_row0, uint64_t* out_rows,
@@ -283,17 +284,18 @@ int cxbwt_build_batch(cxbwt_ctx* ctx, const cxbwt_collection* colls, uint64_t k,
  *
  * A server runs `workers` builds at once, each on its own context (its share
  * of the device budget) and CUDA stream.  Requests queue in arrival order; a
- * free worker takes the oldest one plus every queued request of the same read
- * length that fits its pack cap (requests that arrive while others run join
- * the next pack), builds them together (cxbwt_build_batch) and writes each
- * result into the request's host buffers.  Every result is exactly what
+ * free worker takes the oldest one.  A small one (under 2M suffixes) is
+ * packed with every queued small request of the same read length that fits
+ * the worker's pack cap (requests that arrive while others run join the next
+ * pack) and built with them (cxbwt_build_batch); a larger one is built alone.
+ * Each result is written into the request's host buffers and is exactly what
  * cxbwt_build gives for that request alone. */
 typedef struct cxbwt_server cxbwt_server;
 
 typedef struct {
   uint64_t device_budget_bytes; /* device memory all workers may hold together; 0 = min(120 GB, 90% of free) */
   int device;
-  int workers;                  /* concurrent builds; 0 = 3 */
+  int workers;                  /* concurrent builds; 0 = 2 */
   uint64_t max_pack_suffixes;   /* suffixes built together at most; 0 = derived from the budget */
   int reserved[8];
 } cxbwt_server_options;
@@ -334,7 +336,8 @@ int cxbwt_server_counters(cxbwt_server* s, uint64_t* completed, uint64_t* packs,
  * keeps the fastest in the context for builds of the same maximum read
  * length and size class (N within a factor of two) whose options leave
  * tile_items and algorithm automatic.  Candidates: tiles of 4096 or 8192
- * items x the group plan (reads of at most 528 bases) or the LSD plan.  The
+ * items (2048, 3072 or 4096 when the build carries 64-bit suffix ids) x the
+ * group plan (reads of at most 528 bases) or the LSD plan.  The
  * radix digit is 8 bits (the only width built).  scratch_bwt (ceil(N / 16)
  * words) and scratch_dollar_pos (n_reads, may be NULL) receive the BWT;
  * every candidate produces the same one. */

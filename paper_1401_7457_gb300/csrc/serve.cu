@@ -3,14 +3,18 @@
 // A server owns W workers; each worker is a host thread with its own context
 // (device workspace, within budget / W) and its own CUDA stream, so up to W
 // builds are on the GPU at once and overlap there.  Requests queue in arrival
-// order.  A free worker takes the oldest request and, while they fit its pack
-// cap, every other queued request with the same read length (requests that
-// arrived while others were running join the next pack), copies their reads
-// to the device, builds them as one batch (cxbwt_build_batch: one sort for the
-// pack, split by collection), and streams each BWT back to the caller's host
-// buffers.  Each request's result is exactly what cxbwt_build gives for it
-// alone.  Admission is by device memory: a worker's context never holds more
-// than its share of the budget (larger requests are built in slices).
+// order.  A free worker takes the oldest request.  When that one is small
+// (under kPackRows suffixes, where a lone build is bound by launches and
+// histograms rather than by the sort), the worker also takes every other
+// queued small request of the same read length that fits its pack cap
+// (requests that arrived while others were running join the next pack) and
+// builds them as one batch (cxbwt_build_batch: one sort for the pack, split
+// by collection); a larger request is built alone (cxbwt_build), so it never
+// waits behind another one in the same worker while a second worker is free.
+// Each BWT streams back to the caller's host buffers, and each request's
+// result is exactly what cxbwt_build gives for it alone.  Admission is by
+// device memory: a worker's context never holds more than its share of the
+// budget (larger requests are built in slices).
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -29,6 +33,10 @@ using namespace cxbwt::host;
 namespace {
 
 using Clock = std::chrono::steady_clock;
+
+// Requests below this many suffixes are packed with others of their read
+// length (the batch path packs collections below the same size).
+constexpr uint64_t kPackRows = uint64_t(2) << 20;
 
 struct Req {
   cxbwt_request r{};
@@ -77,10 +85,10 @@ void worker_loop(cxbwt_server* s, int w) {
       s->queue.pop_front();
       take.push_back(first);
       uint64_t rows = first->N;
-      if (first->uniform) {
+      if (first->uniform && first->N < kPackRows) {
         for (auto it = s->queue.begin(); it != s->queue.end() && take.size() < kMaxPackCollections - 1;) {
           Req* q = *it;
-          if (q->uniform && q->L == first->L && rows + q->N <= s->pack_cap) {
+          if (q->uniform && q->L == first->L && q->N < kPackRows && rows + q->N <= s->pack_cap) {
             rows += q->N;
             take.push_back(q);
             it = s->queue.erase(it);
@@ -103,7 +111,9 @@ void worker_loop(cxbwt_server* s, int w) {
       c.out_counts = q->r.out_counts;
       colls.push_back(c);
     }
-    int status = cxbwt_build_batch(ctx, colls.data(), colls.size(), st);
+    int status = take.size() == 1 ? cxbwt_build(ctx, colls[0].reads_2bit, colls[0].n_reads, colls[0].lens,
+                                                colls[0].out_bwt, colls[0].out_dollar_pos, colls[0].out_counts, st)
+                                  : cxbwt_build_batch(ctx, colls.data(), colls.size(), st);
     if (status == CXBWT_OK) {
       const cudaError_t e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) status = CXBWT_ECUDA;
@@ -131,7 +141,9 @@ extern "C" {
 void cxbwt_default_server_options(cxbwt_server_options* o) {
   if (!o) return;
   std::memset(o, 0, sizeof *o);
-  o->workers = 3;
+  // Two concurrent builds: on the served workload (requests of 5M to 750M
+  // suffixes) a third one raised p99 latency at every load (measured).
+  o->workers = 2;
 }
 
 int cxbwt_server_create(cxbwt_server** out, const cxbwt_server_options* opt) {
@@ -140,7 +152,7 @@ int cxbwt_server_create(cxbwt_server** out, const cxbwt_server_options* opt) {
   cxbwt_server_options o;
   cxbwt_default_server_options(&o);
   if (opt) o = *opt;
-  if (o.workers <= 0) o.workers = 3;
+  if (o.workers <= 0) o.workers = 2;
   if (o.workers > 16) return CXBWT_EINVAL;
   if (cudaSetDevice(o.device) != cudaSuccess) {
     cudaGetLastError();
@@ -161,6 +173,7 @@ int cxbwt_server_create(cxbwt_server** out, const cxbwt_server_options* opt) {
     cxbwt_default_options(&co);
     co.device = o.device;
     co.device_budget_bytes = share;
+    co.batch_workers = 1;  // the server's workers are the concurrency; a pack is built by its own worker
     cxbwt_ctx* c = nullptr;
     int st = cxbwt_create(&c, &co);
     cudaStream_t stream = nullptr;
