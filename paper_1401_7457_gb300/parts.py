@@ -14,8 +14,8 @@ and a part is a range of whole buckets, built on the device by
 * ``build_sharded``: one part per rank of a ``torch.distributed`` group.  Each
   rank computes the bucket counts itself (no exchange needed for the plan),
   builds its part, and the parts are gathered to rank 0 and merged: the only
-  exchange is that ordered gather (plus nothing else: the symbol counts add,
-  the ``$`` rows merge by element-wise minimum, the packed words by OR).
+  exchange is that ordered gather, as tensors (the symbol counts add, the
+  ``$`` rows merge by element-wise minimum, the packed words by OR).
 * ``build_rounds``: the parts one after another into files (the packed B_R
   and the ``$`` rows, as memory maps, so host memory holds one part at a
   time), with a checkpoint after every part: an interrupted build resumes at
@@ -81,24 +81,62 @@ def build_part_host(ctx, reads_2bit, lens, part: Part, stream=None, bucket_count
             _host(c).view(np.uint64))
 
 
-def gather_parts(local, part: Part, n_symbols: int, n_reads: int, group=None):
-    """Gather every rank's (part, words, dollar_pos, counts) to rank 0 and merge
-    them there; returns the full (bwt, dollar_pos, counts) on rank 0, None on
-    the other ranks.  This is the only exchange of a sharded build."""
+def gather_parts(local, part: Part, n_symbols: int, n_reads: int, plan=None, group=None):
+    """Gather every rank's part outputs (words, dollar_pos, counts) to rank 0
+    and merge them there; returns the full (bwt, dollar_pos, counts) on rank 0,
+    None on the other ranks.  This is the only exchange of a sharded build,
+    and it moves tensors (on the GPU under NCCL, on the host under gloo):
+
+    * the $ rows by an element-wise MIN reduction (a read's row is set in the
+      one part that holds it; the others hold no row, sent as the largest
+      int64),
+    * the symbol counts by a SUM reduction,
+    * each part's packed words by a send to rank 0, whose sizes rank 0 knows
+      from the plan (``plan``: every rank's Part, as ``plan_parts`` gives it;
+      without it the sizes are exchanged first).
+    """
+    import torch
     import torch.distributed as dist
 
     rank = dist.get_rank(group)
     world = dist.get_world_size(group)
-    words, dollar_pos, counts = local
-    payload = (part, np.asarray(words), np.asarray(dollar_pos), np.asarray(counts))
-    got = [None] * world if rank == 0 else None
     dst = dist.get_global_rank(group, 0) if group is not None else 0
-    dist.gather_object(payload, got, dst=dst, group=group)
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend(group) == "nccl" else torch.device("cpu")
+    words, dollar_pos, counts = local
+    d = np.asarray(dollar_pos).view(np.uint64).copy()
+    big = np.uint64(np.iinfo(np.int64).max)
+    d[d == NO_ROW] = big
+    dt = torch.from_numpy(d.view(np.int64)).to(dev)
+    dist.reduce(dt, dst=dst, op=dist.ReduceOp.MIN, group=group)
+    ct = torch.from_numpy(np.asarray(counts).view(np.uint64).astype(np.int64)).to(dev)
+    dist.reduce(ct, dst=dst, op=dist.ReduceOp.SUM, group=group)
+    if plan is None:
+        # Every rank's (row0, rows), so that rank 0 can size its receives.
+        mine = torch.tensor([part.lo, part.hi, part.row0, part.rows], dtype=torch.int64, device=dev)
+        allp = [torch.empty_like(mine) for _ in range(world)]
+        dist.all_gather(allp, mine, group=group)
+        plan = [Part(*(int(x) for x in t.cpu().tolist())) for t in allp]
     if rank != 0:
+        if part.rows:
+            w = np.ascontiguousarray(np.asarray(words, dtype=np.uint32)[: binding.part_words(part.row0, part.rows)])
+            dist.send(torch.from_numpy(w.view(np.int32)).to(dev), dst=dst, group=group)
         return None
     result = empty_result(n_symbols, n_reads)
-    for p, w, d, c in sorted(got, key=lambda x: x[0].lo):
-        merge_into(result, p, w, d, c)
+    bwt = result[0]
+    if part.rows:
+        binding.merge_part(bwt, np.asarray(words, dtype=np.uint32), part.row0, part.rows)
+    for r in range(1, world):
+        p = plan[r]
+        if not p.rows:
+            continue
+        buf = torch.empty(binding.part_words(p.row0, p.rows), dtype=torch.int32, device=dev)
+        src = dist.get_global_rank(group, r) if group is not None else r
+        dist.recv(buf, src=src, group=group)
+        binding.merge_part(bwt, buf.cpu().numpy().view(np.uint32), p.row0, p.rows)
+    dm = dt.cpu().numpy().view(np.uint64).copy()
+    dm[dm == big] = NO_ROW
+    result[1][:] = dm
+    result[2][:] = ct.cpu().numpy().astype(np.uint64)
     return result
 
 
@@ -114,7 +152,7 @@ def build_sharded(ctx, reads_2bit, lens, group=None, stream=None):
     n_symbols = int(counts.sum())
     n_reads = int(lens.numel() if binding._is_tensor(lens) else np.asarray(lens).size)
     local = build_part_host(ctx, reads_2bit, lens, parts[rank], stream=stream, bucket_counts=counts)
-    return gather_parts(local, parts[rank], n_symbols, n_reads, group=group)
+    return gather_parts(local, parts[rank], n_symbols, n_reads, plan=parts, group=group)
 
 
 def _fingerprint(bucket_counts, n_reads: int, n_rounds: int) -> str:
