@@ -388,10 +388,13 @@ def run_reference(args, rank, world):
 
 def run_batch_bench(args, rank, world):
     """The batched workload: 256 collections (n log-uniform in [10k, 2M], read
-    length from {36, 76, 100, 150}, genome-like reads).  Times cxbwt_build_batch
-    against the plain loop of one cxbwt_build per collection, both on
-    device-resident inputs and outputs.  Prints one JSON line (not the
-    benchmark's default workload)."""
+    length from {36, 76, 100, 150}, genome-like reads).  The autotuner first
+    picks the tile and the sort plan for each (read length, size class) that
+    occurs, on the first collection of that class; then cxbwt_build_batch is
+    timed against the plain loop of one cxbwt_build per collection, both with
+    the tuned plans, on device-resident inputs and outputs.  Every result of
+    both is compared with the oracle's stored digest of its collection.  One
+    JSON line (not the benchmark's default workload)."""
     import torch
 
     from paper_1401_7457_gb300 import binding, build, synth
@@ -400,6 +403,7 @@ def run_batch_bench(args, rank, world):
     specs = synth.batch_specs()
     if args.reads:
         specs = specs[:args.reads]
+    want = oracle_item_digests("batched")
     colls, bases, suffixes = [], 0, 0
     for sp in specs:
         codes, lens = synth.batch_collection(sp)
@@ -413,6 +417,13 @@ def run_batch_bench(args, rank, world):
         suffixes += N
     stream = torch.cuda.current_stream(dev)
     ctx = binding.Context(device=0, budget_bytes=int(args.budget_gb * (1 << 30)))
+    # Autotune each (read length, size class) on its first collection.
+    picks, t0 = {}, time.perf_counter()
+    for sp, c in zip(specs, colls):
+        cls = (sp["length"], (int(c[1].numel()) * (sp["length"] + 1)).bit_length())
+        if cls not in picks:
+            picks[cls] = ctx.autotune(c[0], c[1], c[2], c[3], stream=stream)
+    tune_s = time.perf_counter() - t0
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
     def plain():
@@ -422,10 +433,23 @@ def run_batch_bench(args, rank, world):
     def batched():
         ctx.build_batch(colls, stream=stream)
 
-    out = {}
+    def check():
+        if want is None:
+            return None
+        torch.cuda.synchronize()
+        ok = all(packed_digest(c[2].cpu().numpy().view(np.uint32), c[3].cpu().numpy(), c[4].cpu().numpy()) == d
+                 for c, d in zip(colls, want))
+        for c in colls:
+            for t in c[2:]:
+                t.zero_()
+        return ok
+
+    out, equal = {}, {}
     for name, fn in (("plain", plain), ("batched", batched)):
         for _ in range(max(args.warmup, 1)):
             fn()
+        equal[name] = check()
+        fn()
         torch.cuda.synchronize()
         ts = []
         for _ in range(args.steps):
@@ -436,14 +460,21 @@ def run_batch_bench(args, rank, world):
             torch.cuda.synchronize()
             ts.append(time.perf_counter() - t0)
         out[name] = sum(ts) / len(ts)
+        equal[name] = equal[name] and check() if equal[name] is not None else None
     ctx.close()
+    chosen = {}
+    for (L, cls), t in sorted(picks.items()):
+        k = f"tile {t['tile_items']}, {'groups' if t['algorithm'] == 2 else 'lsd'}"
+        chosen[k] = chosen.get(k, 0) + 1
     line = {"metric": METRIC, "value": bases / out["batched"] / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": out["batched"] * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": f"batched: {len(colls)} collections, {bases:,} bases, {suffixes:,} suffixes",
                        "l2": "flushed between steps", "input": "device-resident"},
             "plain_loop": {"value": bases / out["plain"] / 1e9, "unit": UNIT, "ms_per_step": out["plain"] * 1e3},
-            "speedup_vs_plain_loop": out["plain"] / out["batched"]}
+            "speedup_vs_plain_loop": out["plain"] / out["batched"],
+            "autotune": {"classes": len(picks), "seconds": tune_s, "choices": chosen},
+            "results_equal_oracle": equal}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -481,7 +512,7 @@ def run_serve_bench(args, rank, world):
     * the plain loop: one cxbwt_build at a time, first come first served,
       pinned host buffers;
     * the server: cxbwt_submit at each arrival time (continuous batching,
-      3 workers).
+      2 and 3 workers).
 
     Latency = completion - arrival.  Every result of every run is compared
     with the oracle's stored digest of that request.  One JSON line with
@@ -561,12 +592,7 @@ def run_serve_bench(args, rank, world):
         th.join()
         return lat, time.perf_counter() - t0
 
-    srv = binding.Server(device=0, budget_bytes=budget or (120 << 30), workers=3)
-    warm = srv.submit(inputs[0][0], inputs[0][1], *outs[0])
-    srv.wait(warm)
-    check_and_clear()
-
-    def served_run(arrivals):
+    def served_run(srv, arrivals):
         tickets = [None] * len(inputs)
         t0 = time.perf_counter()
         for i, ((w, lt, N, n), o) in enumerate(zip(inputs, outs)):
@@ -581,31 +607,40 @@ def run_serve_bench(args, rank, world):
 
     p = lambda xs, q: float(np.percentile(np.asarray(xs), q))
     loads = {}
+    traces = []
     for j, f in enumerate((0.5, 0.8, 1.0, 1.5)):
         trace_seed = 50 + j
         rng = np.random.default_rng(trace_seed)
         gaps = rng.exponential(1.0 / (f * capacity), size=len(inputs))
-        arrivals = np.cumsum(gaps) - gaps[0]  # the first request arrives at time 0
+        traces.append((f, trace_seed, np.cumsum(gaps) - gaps[0]))  # the first request arrives at time 0
+    for f, trace_seed, arrivals in traces:
         lat_p, span_p = plain_run(arrivals)
         ok_p = check_and_clear()
-        before = srv.counters()["packs"]
-        lat_s, span_s = served_run(arrivals)
-        ok_s = check_and_clear()
         loads[f"{f:g}x"] = {
             "arrival_rate_per_s": f * capacity, "trace_seed": trace_seed,
             "plain_loop": {"p50_ms": p(lat_p, 50), "p99_ms": p(lat_p, 99), "gbase_per_s": total_bases / span_p / 1e9,
-                           "span_s": span_p, "results_equal_oracle": ok_p},
-            "served": {"p50_ms": p(lat_s, 50), "p99_ms": p(lat_s, 99), "gbase_per_s": total_bases / span_s / 1e9,
-                       "span_s": span_s, "packs": srv.counters()["packs"] - before, "results_equal_oracle": ok_s}}
-    srv.close()
+                           "span_s": span_p, "results_equal_oracle": ok_p}}
     ctx.close()
-    sat = loads["1.5x"]
-    line = {"metric": METRIC, "value": sat["served"]["gbase_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1,
-            "warmup": 1, "ms_per_step": sat["served"]["span_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+    for workers in (2, 3):
+        srv = binding.Server(device=0, budget_bytes=budget or (120 << 30), workers=workers)
+        warm = srv.submit(inputs[0][0], inputs[0][1], *outs[0])
+        srv.wait(warm)
+        check_and_clear()
+        for f, _, arrivals in traces:
+            before = srv.counters()["packs"]
+            lat_s, span_s = served_run(srv, arrivals)
+            ok_s = check_and_clear()
+            loads[f"{f:g}x"][f"served_{workers}_workers"] = {
+                "p50_ms": p(lat_s, 50), "p99_ms": p(lat_s, 99), "gbase_per_s": total_bases / span_s / 1e9,
+                "span_s": span_s, "builds": srv.counters()["packs"] - before, "results_equal_oracle": ok_s}
+        srv.close()
+    sat = loads["1.5x"]["served_2_workers"]
+    line = {"metric": METRIC, "value": sat["gbase_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": sat["span_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": f"served: {len(inputs)} requests, {total_bases:,} bases, Poisson arrivals at 0.5, "
                                    f"0.8, 1.0 and 1.5x the plain loop's measured {capacity:.1f} requests/s",
-                       "workers": 3, "value": "served Gbase/s at 1.5x (saturated)"},
+                       "workers": [2, 3], "value": "served Gbase/s at 1.5x (saturated), 2 workers (the default)"},
             "loads": loads, "plain_alone_equal_oracle": alone_ok, "oracle_digests": want is not None}
     print(json.dumps(line), flush=True)
     return 0
@@ -730,6 +765,88 @@ def run_parts_bench(args, rank, world):
     return 0
 
 
+def run_sharded_bench(args, rank, world):
+    """Bucket-range parts of one collection across the ranks (Section 3.3):
+    every rank holds the whole read store, counts the 8-base buckets itself,
+    and builds the part of B_R made of its range of buckets (about N / world
+    suffixes); one step = every rank's part, device-resident input and output,
+    timed with CUDA events (max over ranks).  ``value`` = the collection's
+    bases / that time: strong scaling, the work is one collection whatever
+    the number of ranks.  ``e2e`` = parts.build_sharded end to end (the count,
+    the part, its copy to the host and the gather of every part to rank 0 as
+    tensors), wall time max over ranks.  One JSON line on rank 0."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1401_7457_gb300 import binding, build, parts
+
+    if world > 1:
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    build.build()
+    name = args.shard_workload
+    desc, codes, lens = load_workload(name, 0, args.reads)  # the same collection on every rank
+    words = binding.pack_codes(codes)
+    del codes
+    n, bases = lens.size, int(lens.sum())
+    d_words = torch.from_numpy(words.view(np.int32)).to(dev)
+    d_lens = torch.from_numpy(lens.view(np.int32)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = binding.Context(device=local, budget_bytes=int(args.budget_gb * (1 << 30)))
+    counts = ctx.bucket_counts(d_words, d_lens, stream=stream)
+    plan = parts.plan_parts(counts, world)
+    mine = plan[rank]
+    out = ctx.build_part(d_words, d_lens, mine.lo, mine.hi, mine.row0, mine.rows, stream=stream, bucket_counts=counts)
+    for _ in range(max(args.warmup, 3) - 1):
+        ctx.build_part(d_words, d_lens, mine.lo, mine.hi, mine.row0, mine.rows, *out, stream=stream,
+                       bucket_counts=counts)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    ms = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.build_part(d_words, d_lens, mine.lo, mine.hi, mine.row0, mine.rows, *out, stream=stream,
+                       bucket_counts=counts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    value, total_ms = aggregate(dist, sum(ms), bases / world, world, args.steps)
+    # End to end: the whole sharded build through parts.build_sharded.
+    t_e2e = []
+    for _ in range(max(1, min(args.steps, 3))):
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = parts.build_sharded(ctx, d_words, d_lens, stream=stream) if world > 1 else \
+            parts.build_part_host(ctx, d_words, d_lens, mine, stream=stream)
+        t_e2e.append(time.perf_counter() - t0)
+        del res
+    e2e_value, e2e_ms = aggregate(dist, sum(t_e2e) * 1e3, bases / world, world, len(t_e2e))
+    ctx.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "u64" if id_bytes(n, int(lens.max()), (bases + 15) // 16 * 4) == 8 else "u32",
+                "data": "synthetic",
+                "config": {"workload": "bucket-range parts of one collection, one per rank: " + desc.format(n=n, N=bases + n),
+                           "parts": [{"lo": p.lo, "hi": p.hi, "rows": p.rows} for p in plan],
+                           "l2": "flushed between steps (512 MB write outside the events)"},
+                "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms / len(t_e2e),
+                        "h2d_bytes_per_step": 0, "d2h_bytes_per_step": (bases + n) // 4 + 8 * n,
+                        "path": "parts.build_sharded: bucket counts, the part, its copy to the host, gather to rank 0"}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -743,8 +860,13 @@ def main():
     ap.add_argument("--no-config2", action="store_true", help="skip the genome-like measurement (config2 key)")
     ap.add_argument("--reads", type=int, default=0,
                     help="reads per GPU (0: the workload's own size; smaller only for profiling captures)")
-    ap.add_argument("--workload", default="repeat-rich", choices=sorted(WORKLOADS) + ["batch", "serve", "length", "parts"],
+    ap.add_argument("--shard-workload", default="repeat-rich", choices=sorted(WORKLOADS),
+                    help="the collection --workload sharded splits across the ranks")
+    ap.add_argument("--workload", default="repeat-rich",
+                    choices=sorted(WORKLOADS) + ["batch", "serve", "length", "parts", "sharded"],
                     help="repeat-rich is the benchmark; the others are the other workloads, timed for reference")
+    ap.add_argument("--tile-items", type=int, default=0,
+                    help="items per radix tile of the benchmark's contexts (0: the library's choice)")
     ap.add_argument("--plan-flags", type=int, default=0,
                     help="CXBWT_PLAN_* bits of the benchmark's contexts (1: 64-bit ids; for profiling captures)")
     ap.add_argument("--budget-gb", type=float, default=0.0,
@@ -763,6 +885,8 @@ def main():
         return run_length_bench(args, rank, world)
     if args.workload == "parts":
         return run_parts_bench(args, rank, world)
+    if args.workload == "sharded":
+        return run_sharded_bench(args, rank, world)
 
     import torch
     import torch.distributed as dist
@@ -845,7 +969,8 @@ def measure(args, dist, world, local, dev, desc, codes, lens, steps, e2e_steps):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    ctx = binding.Context(device=local, timing=True, budget_bytes=budget, plan_flags=args.plan_flags)
+    ctx = binding.Context(device=local, timing=True, budget_bytes=budget, plan_flags=args.plan_flags,
+                          tile_items=args.tile_items)
 
     def step():
         ctx.build(d_words, d_lens, d_bwt, d_dpos, d_cnt, stream=stream)
@@ -902,7 +1027,7 @@ def measure(args, dist, world, local, dev, desc, codes, lens, steps, e2e_steps):
     h_bwt = torch.empty(n_words, dtype=torch.int32).pin_memory()
     h_dpos = torch.empty(n, dtype=torch.int64).pin_memory()
     h_cnt = torch.zeros(5, dtype=torch.int64).pin_memory()
-    ctx2 = binding.Context(device=local, budget_bytes=budget, plan_flags=args.plan_flags)
+    ctx2 = binding.Context(device=local, budget_bytes=budget, plan_flags=args.plan_flags, tile_items=args.tile_items)
     for _ in range(2):
         ctx2.build(h_words, h_lens, h_bwt, h_dpos, h_cnt, stream=stream)
     ctx2.reset_stats()
