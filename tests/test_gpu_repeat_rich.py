@@ -4,9 +4,12 @@ device-memory-bounded slices with the BWT streamed to pinned host memory.
 
 * one tenth of the workload (5M reads, 505M suffixes): every symbol, $ row and
   count against the oracle's full sort;
-* the full workload (50M reads x 100 bp, 5.05G suffixes, 64-bit suffix ids):
-  exact symbol counts, the first n symbols, every $ row, and sampled rows
-  whose suffix the oracle ranks one by one.
+* the full workload (50M reads x 100 bp, 5.05G suffixes, 64-bit suffix ids,
+  at least three slices): the whole result (every symbol, $ row and count)
+  against the digest of the oracle's result, stored by
+  tests/golden/make_oracle_digests.py (the oracle sorted it one range of
+  prefix buckets at a time); then exact symbol counts, the first n symbols,
+  every $ row, and sampled rows whose suffix the oracle ranks one by one.
 """
 import os
 
@@ -14,6 +17,7 @@ import numpy as np
 import pytest
 
 import oracle
+import pins
 from gpu_helpers import assert_same  # noqa: F401
 from paper_1401_7457_gb300 import synth
 
@@ -64,14 +68,37 @@ def test_repeat_rich_tenth_full_parity():
     assert_same(got, ref)
 
 
-def test_repeat_rich_full_size_sampled():
+@pytest.fixture(scope="module")
+def full_build():
+    """The whole repeat-rich workload, built once in device-memory-bounded
+    slices (a third of the suffixes each) with the suffix order on the device."""
     _need_gpu()
     codes, lens = synth.repeat_rich()
-    n = lens.size
-    N = int(lens.sum()) + n
+    N = int(lens.sum()) + lens.size
     assert N == 5_050_000_000
     budget = (2 << 30) + int(0.5 * N) + int(25.25 * N / 3)
     bwt, dpos, cnt, d_sa, st = build_sliced(codes, lens, budget, want_sa_device=True)
+    yield codes, lens, bwt, dpos, cnt, d_sa, st
+    del d_sa
+    torch.cuda.empty_cache()
+
+
+def test_repeat_rich_full_size_digest(full_build):
+    """Every symbol, $ row and count of the 5.05G-suffix build equals the
+    oracle's result (its stored digest)."""
+    codes, lens, bwt, dpos, cnt, _, st = full_build
+    want = pins.read_oracle_digests()["repeat-rich"]
+    if pins.input_digest(codes, lens) != want["input_sha256"]:
+        pytest.skip("this numpy draws another repeat-rich collection than the one the digest was made from")
+    assert st["slices"] >= 3, st
+    assert bwt.size == (want["n_symbols"] + 15) // 16
+    assert pins.packed_result_digest(bwt, dpos, cnt) == want["packed_sha256"]
+
+
+def test_repeat_rich_full_size_sampled(full_build):
+    codes, lens, bwt, dpos, cnt, d_sa, st = full_build
+    n = lens.size
+    N = int(lens.sum()) + n
     assert st["slices"] >= 3, st
     # Exact counts: the input composition plus n terminators.
     comp = np.bincount(codes, minlength=4)
