@@ -39,9 +39,11 @@ constexpr int kChunk = 256;  // rows scanned per warp task
 // Bases [c0, c0 + 16*NW) of suffix s (A-padded past the read end) as NW words,
 // from the NW + 1 store words they span (4-byte loads: fewer registers held
 // per load in flight than 16-byte chunks, and no realignment of the chunks).
-// No branch depends on the suffix: a window past the read's end reads the
-// read's first words and is masked to zero, and the words past the end are
-// masked the same way, so the lanes of a warp stay together.
+// Only the store words that hold some of the suffix's bases are loaded (the
+// loads are predicated, not branched around, so the lanes of a warp stay
+// together): a suffix near its read's end, or one that ends inside the
+// first window (no load at all), moves fewer DRAM sectors when the store is
+// out of L2.  The words past the read's end are masked to zero.
 template <int NW>
 __device__ __forceinline__ void gather_words(const ReadIndex& R, const Suffix& s, uint32_t c0, uint32_t (&w)[NW]) {
   const uint32_t rel = s.k + c0;
@@ -50,9 +52,11 @@ __device__ __forceinline__ void gather_words(const ReadIndex& R, const Suffix& s
   const uint64_t q = s.off + (inside ? rel : 0u);
   const uint64_t w0 = q >> 4;
   const uint32_t sh = uint32_t(q & 15u) * 2u;
+  // Store words holding bases q .. q + rem - 1 (none when rem == 0).
+  const uint32_t n_load = rem ? uint32_t(((q + rem - 1) >> 4) - w0) + 1u : 0u;
   uint32_t b[NW + 1];
 #pragma unroll
-  for (int i = 0; i <= NW; ++i) b[i] = load_word(R, w0 + i);
+  for (int i = 0; i <= NW; ++i) b[i] = uint32_t(i) < n_load ? load_word(R, w0 + i) : 0u;
 #pragma unroll
   for (int i = 0; i < NW; ++i) {
     const uint32_t need = 16u * i;

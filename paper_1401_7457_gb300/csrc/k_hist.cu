@@ -198,10 +198,22 @@ __global__ void __launch_bounds__(kKeyHistThreads) k_key_hist(const uint32_t* __
   __syncthreads();
   uint32_t* mine = sk + (threadIdx.x >> 5) * 4 * kRadix;
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-  for (uint64_t r = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < n; r += stride) {
-    const uint32_t k = __ldg(keys + r);
+  // Eight independent loads in flight per thread (coalesced across the
+  // warp for each of them), then their 32 counter increments.
+  constexpr int kUnroll = 8;
+  for (uint64_t r0 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; r0 < n; r0 += stride * kUnroll) {
+    uint32_t k[kUnroll];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) atomicAdd(&mine[j * kRadix + ((k >> (24 - 8 * j)) & 255u)], 1u);
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint64_t r = r0 + uint64_t(u) * stride;
+      k[u] = r < n ? __ldg(keys + r) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      if (r0 + uint64_t(u) * stride >= n) break;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) atomicAdd(&mine[j * kRadix + ((k[u] >> (24 - 8 * j)) & 255u)], 1u);
+    }
   }
   __syncthreads();
   for (uint32_t x = threadIdx.x; x < 4 * kRadix; x += blockDim.x) {
@@ -320,7 +332,7 @@ cudaError_t launch_key_hist(const uint32_t* keys, uint64_t n, uint32_t* hist, in
     cudaError_t e = cudaFuncSetAttribute(k_key_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     uint64_t gx = (n + kKeyHistThreads - 1) / kKeyHistThreads;
-    if (gx > uint64_t(2 * sm_count)) gx = 2 * sm_count;
+    if (gx > uint64_t(3 * sm_count)) gx = 3 * sm_count;  // three 64 KB CTAs per SM
     k_key_hist<<<uint32_t(gx), kKeyHistThreads, smem, st>>>(keys, n, hist);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
