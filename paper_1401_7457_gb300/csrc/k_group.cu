@@ -312,7 +312,7 @@ __device__ void finish_long_group(const SegArgs& a, uint32_t gs, uint32_t ge, in
 // tens-fold coverage); with the store in L2 the ranking's instructions
 // dominate and 32-row windows, with fewer of them, are faster (measured).
 template <int NW, class V, int SPAN>
-__global__ void __launch_bounds__(256) k_segsort_warp(const SegArgs a) {
+__device__ __forceinline__ void segsort_warp_body(const SegArgs& a) {
   using H = typename Heads<SPAN>::T;
   const int lane = threadIdx.x & 31;
   __shared__ RowWords<NW, SPAN> s_rows[8];
@@ -351,6 +351,22 @@ __global__ void __launch_bounds__(256) k_segsort_warp(const SegArgs a) {
       cur += n_rows;
     }
   }
+}
+
+template <int NW, class V>
+__global__ void __launch_bounds__(256) k_segsort_warp(const SegArgs a) {
+  segsort_warp_body<NW, V, 32>(a);
+}
+
+// The 64-row windows wait on DRAM gathers: resident warps hide that wait, so
+// the registers are capped for kWideBlocks CTAs of 256 threads per SM (40
+// registers; the 16 KB of shared rows per CTA allow more CTAs).  Measured on
+// 5.05G repeat-rich suffixes: 145.4 ms per build uncapped (45 registers, 5
+// CTAs), 137.1 ms for 6 CTAs, 141.4 ms for 8 (32 registers, more spilled).
+constexpr int kWideBlocks = 6;
+template <int NW, class V>
+__global__ void __launch_bounds__(256, kWideBlocks) k_segsort_warp_wide(const SegArgs a) {
+  segsort_warp_body<NW, V, 64>(a);
 }
 
 // Shared-memory bitonic sort of one listed group per CTA, for groups of up to
@@ -497,8 +513,8 @@ cudaError_t launch_nw(const SegArgs& a, int sm_count, bool wide, cudaStream_t st
   if (blocks > cap) blocks = cap;
   if (blocks == 0) blocks = 1;
   // Rows of the widest keys (long reads) would not fit twice in shared memory.
-  if (wide && NW <= 16) k_segsort_warp<NW, V, (NW <= 16 ? 64 : 32)><<<blocks, 256, 0, st>>>(a);
-  else k_segsort_warp<NW, V, 32><<<blocks, 256, 0, st>>>(a);
+  if (wide && NW <= 16) k_segsort_warp_wide<NW, V><<<blocks, 256, 0, st>>>(a);
+  else k_segsort_warp<NW, V><<<blocks, 256, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = launch_cta_nw<NW, V, kSmallCta, 128>(a, uint32_t(sm_count) * 16, a.cta_list, a.counts + 0, a.cta_cap, 1,
