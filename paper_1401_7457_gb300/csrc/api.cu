@@ -59,7 +59,8 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
 
   // ---- digit bases -----------------------------------------------------------
   // whole: rows 0..d_sorted-1 = char digits d, rows D.. = length digits.
-  // slice: rows 0 = suffix length, 1..4 = window-0 digits (most significant first).
+  // slice: row 0 = suffix length (its low byte), rows 1..4 = window-0 digits
+  // (most significant first), row 5 = the high byte of the suffix length.
   if (sl.pregen) {
     // The slice's first windows are listed already: count their digits (rows 1..4).
     CX_CUDA(c, cudaMemsetAsync(r.base + kRadix, 0, 4 * kRadix * 4, st));

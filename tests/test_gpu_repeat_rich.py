@@ -95,6 +95,33 @@ def test_repeat_rich_full_size_digest(full_build):
     assert pins.packed_result_digest(bwt, dpos, cnt) == want["packed_sha256"]
 
 
+def test_repeat_rich_default_budget_digest(full_build):
+    """The build as the benchmark runs it: the default budget, two slices
+    (N > 2^32 rows) listed by one pass, device-resident input and outputs.
+    The whole result equals the oracle's."""
+    from paper_1401_7457_gb300 import binding
+    codes, lens = full_build[0], full_build[1]
+    want = pins.read_oracle_digests()["repeat-rich"]
+    if pins.input_digest(codes, lens) != want["input_sha256"]:
+        pytest.skip("this numpy draws another repeat-rich collection than the one the digest was made from")
+    dev = torch.device("cuda:0")
+    N = int(lens.sum()) + lens.size
+    d_words = torch.from_numpy(binding.pack_codes(codes).view(np.int32)).to(dev)
+    d_lens = torch.from_numpy(lens.view(np.int32)).to(dev)
+    bwt = torch.empty((N + 15) // 16, dtype=torch.int32, device=dev)
+    dpos = torch.empty(lens.size, dtype=torch.int64, device=dev)
+    cnt = torch.zeros(5, dtype=torch.int64, device=dev)
+    with binding.Context(device=0) as c:
+        c.build(d_words, d_lens, bwt, dpos, cnt)
+        st = c.stats()
+    assert st["slices"] == 2 and st["sort_pass_launches"] == 9, st  # one listing pass, 4 window passes per slice
+    got = pins.packed_result_digest(bwt.cpu().numpy().view(np.uint32), dpos.cpu().numpy().view(np.uint64),
+                                    cnt.cpu().numpy().view(np.uint64))
+    del d_words, d_lens, bwt, dpos, cnt
+    torch.cuda.empty_cache()
+    assert got == want["packed_sha256"]
+
+
 def test_repeat_rich_full_size_sampled(full_build):
     codes, lens, bwt, dpos, cnt, d_sa, st = full_build
     n = lens.size
