@@ -36,14 +36,25 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const EmitArgs a) {
     const bool whole = g0 >= a.row0 && min(g0 + 16, a.n_total) <= end;
     V v[16];
     // 16-byte loads only when all 16 rows are in the slice and the address is
-    // 16-byte aligned (a collection inside a pack may start at any row).
+    // 16-byte aligned (a collection inside a pack, or a slice's part of the
+    // listed rows, may start at any row).
     const bool full16 = g0 >= a.row0 && g0 + 16 <= end;
-    if (full16 && sizeof(V) == 4 && (reinterpret_cast<uintptr_t>(sa + (g0 - a.row0)) & 15u) == 0) {
+    const bool aligned16 = (reinterpret_cast<uintptr_t>(sa + (g0 - a.row0)) & 15u) == 0;
+    if (full16 && aligned16 && sizeof(V) == 4) {
       const uint4* p = reinterpret_cast<const uint4*>(sa + (g0 - a.row0));
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const uint4 x = __ldg(p + q);
         v[4 * q] = V(x.x); v[4 * q + 1] = V(x.y); v[4 * q + 2] = V(x.z); v[4 * q + 3] = V(x.w);
+      }
+    } else if (full16 && aligned16 && sizeof(V) == 8) {
+      // Two 64-bit ids per 16-byte load (little-endian halves).
+      const uint4* p = reinterpret_cast<const uint4*>(sa + (g0 - a.row0));
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const uint4 x = __ldg(p + q);
+        v[2 * q] = V((uint64_t(x.y) << 32) | x.x);
+        v[2 * q + 1] = V((uint64_t(x.w) << 32) | x.z);
       }
     } else {
 #pragma unroll
