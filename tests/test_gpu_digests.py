@@ -66,3 +66,27 @@ def test_batched_workload_digests():
            if pins.packed_result_digest(cl[2].cpu().numpy().view(np.uint32), cl[3].cpu().numpy().view(np.uint64),
                                         cl[4].cpu().numpy().view(np.uint64)) != it["packed_sha256"]]
     assert not bad, f"collections {bad[:10]} differ from the oracle"
+def test_served_workload_digests():
+    """All 256 requests of the served workload (34.3 Gbase) queued on a
+    server at once (2 workers, each request built alone as its worker frees
+    up: every one is above the size packs are made of): each result, written
+    to pinned host buffers, is the oracle's."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1401_7457_gb300 import binding
+    items = pins.read_oracle_digests()["served"]["items"]
+    reqs, outs = [], []
+    for words, lens in _packed_inputs("served", items):
+        N = int(lens.sum()) + lens.size
+        reqs.append((torch.from_numpy(words.view(np.int32)).pin_memory(), torch.from_numpy(lens.view(np.int32)).pin_memory()))
+        outs.append((torch.zeros((N + 15) // 16, dtype=torch.int32).pin_memory(),
+                     torch.zeros(lens.size, dtype=torch.int64).pin_memory(), torch.zeros(5, dtype=torch.int64).pin_memory()))
+    with binding.Server(device=0) as srv:
+        tickets = [srv.submit(w, lt, *o) for (w, lt), o in zip(reqs, outs)]
+        for t in tickets:
+            srv.wait(t)
+        assert srv.counters()["completed"] == len(tickets)
+    bad = [j for j, (o, it) in enumerate(zip(outs, items))
+           if pins.packed_result_digest(o[0].numpy().view(np.uint32), o[1].numpy().view(np.uint64),
+                                        o[2].numpy().view(np.uint64)) != it["packed_sha256"]]
+    assert not bad, f"requests {bad[:10]} differ from the oracle"

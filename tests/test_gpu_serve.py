@@ -24,34 +24,36 @@ def requests(k, seed):
 
 
 def test_served_results_match_alone():
+    """Two large requests (built alone) keep the server's workers busy while
+    41 small ones queue behind them; the small ones of one read length are
+    then packed and built together.  Every small result equals the oracle's
+    and its own solo build; the large ones equal their solo builds."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1401_7457_gb300 import binding
+    blockers = [synth.uniform_reads(3_000_000, 100, 31 + b) for b in range(2)]  # 303M suffixes each
     reqs = requests(40, 21)
     reqs.insert(7, synth.mixed_length_reads(2000, 30, 150, 99))  # built alone inside a worker
-    outs = []
-    with binding.Server(device=0, workers=3) as srv:
-        tickets = []
-        for codes, lens in reqs:
-            words = binding.pack_codes(codes)
-            N = int(lens.sum()) + lens.size
-            bwt = np.zeros((N + 15) // 16, dtype=np.uint32)
-            dpos = np.zeros(lens.size, dtype=np.uint64)
-            cnt = np.zeros(5, dtype=np.uint64)
-            tickets.append(srv.submit(words, lens, bwt, dpos, cnt))
-            outs.append((N, bwt, dpos, cnt))
+    prepared = []
+    for codes, lens in blockers + reqs:
+        N = int(lens.sum()) + lens.size
+        prepared.append((binding.pack_codes(codes), lens, N, np.zeros((N + 15) // 16, dtype=np.uint32),
+                         np.zeros(lens.size, dtype=np.uint64), np.zeros(5, dtype=np.uint64)))
+    with binding.Server(device=0, workers=2) as srv:
+        tickets = [srv.submit(w, ln, b, d, c) for (w, ln, _, b, d, c) in prepared]
         for t in tickets:
             srv.wait(t)
         lat = [srv.times(t)[1] for t in tickets]
         counters = srv.counters()
-    assert counters["completed"] == len(reqs)
-    assert counters["packs"] < len(reqs)  # requests were built together
+    assert counters["completed"] == len(prepared)
+    assert counters["packs"] < len(prepared)  # small requests were built together
     assert all(x > 0 for x in lat)
     with binding.Context(device=0) as ctx:
-        for (codes, lens), (N, bwt, dpos, cnt) in zip(reqs, outs):
-            got = {"bwt": binding.unpack_ascii(bwt, dpos, N), "dollar_pos": dpos, "counts": cnt}
-            assert_same(got, oracle_of(codes, lens))
-            b, d, c = ctx.build(binding.pack_codes(codes), lens)
+        for j, ((codes, lens), (w, _, N, bwt, dpos, cnt)) in enumerate(zip(blockers + reqs, prepared)):
+            if j >= len(blockers):
+                got = {"bwt": binding.unpack_ascii(bwt, dpos, N), "dollar_pos": dpos, "counts": cnt}
+                assert_same(got, oracle_of(codes, lens))
+            b, d, c = ctx.build(w, lens)
             assert np.array_equal(b, bwt) and np.array_equal(d, dpos) and np.array_equal(c, cnt)
 
 
