@@ -105,6 +105,10 @@ typedef struct {
  *                gathers nothing from the store; by default only when the
  *                store is larger than 64 MB (out of L2). */
 #define CXBWT_PLAN_CARRY_BASE 8
+/*  NO_PREFETCH - carried-key digit passes do not ask for their tiles to be
+ *                read into L2 ahead of the CTAs that sort them (by default
+ *                they do when their arrays are 16-byte aligned). */
+#define CXBWT_PLAN_NO_PREFETCH 16
 /* Test hook for failure handling: in the first digit pass of a build, tile 0
  * does not publish its counts, so tile 1's look-back wait runs out (after
  * wait_limit_ms).  The build then returns CXBWT_ETIMEOUT with unspecified

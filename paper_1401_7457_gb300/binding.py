@@ -334,7 +334,7 @@ class Context:
     """One cxbwt context (device workspace + bookkeeping) on one device."""
 
     ALGO_AUTO, ALGO_LSD, ALGO_GROUPS = 0, 1, 2
-    PLAN_ID64, PLAN_READ_MAJOR, PLAN_TEST_STALL, PLAN_CARRY_BASE = 1, 2, 4, 8
+    PLAN_ID64, PLAN_READ_MAJOR, PLAN_TEST_STALL, PLAN_CARRY_BASE, PLAN_NO_PREFETCH = 1, 2, 4, 8, 16
 
     def __init__(self, device: int = 0, budget_bytes: int = 0, async_: bool = False, timing: bool = False,
                  tile_items: int = 0, algorithm: int = 0, plan_flags: int = 0, batch_workers: int = 0,

@@ -55,6 +55,7 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
   a.timeout_ns = c->opt.wait_limit_ms > 0 ? uint64_t(c->opt.wait_limit_ms) * 1000000ull : kTimeoutNs;
   a.key_lo = sl.key_lo;
   a.key_last = uint32_t(sl.key_hi - 1 - sl.key_lo);  // the offset of its last key (a part may span every key)
+  a.prefetch = (c->opt.plan_flags & CXBWT_PLAN_NO_PREFETCH) ? 0u : 1u;
   const uint32_t d_sorted = std::min<uint32_t>(pl.D, 4 * (pl.w_last + 1));
 
   // ---- digit bases -----------------------------------------------------------
@@ -332,8 +333,8 @@ int split_pass(cxbwt_ctx* c, Run& r, const std::vector<Slice>& slices, const std
   a.digit_base = d_sbase;
   a.split_of = d_split;
   for (uint32_t si = 0; si < S; ++si) {
-    a.split_vals[si] = vptr(c->vals[0].p, pl.idb, slices[si].row0);
-    a.split_keys[si] = static_cast<uint32_t*>(c->keys[0].p) + slices[si].row0;
+    a.split_vals[si] = vptr(c->vals[0].p, pl.idb, slices[si].arr0);
+    a.split_keys[si] = static_cast<uint32_t*>(c->keys[0].p) + slices[si].arr0;
     a.split_rows[si] = slices[si].rows;
   }
   a.epoch = ++c->epoch;
@@ -720,14 +721,22 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   bool split = false;
   if (!part && slices.size() > 1 && slices.size() <= kMaxSplit && pl.uniform && r.bucket_bits == 8 && !refined &&
       !P_host.empty() && slices.size() * (pl.Lmax + 1) <= uint64_t(kRadix)) {
-    const uint64_t need = (pl.N + max_rows) * uint64_t(pl.idb + 4) +
+    const uint64_t need = (pl.N + 4 * slices.size() + max_rows) * uint64_t(pl.idb + 4) +
                           uint64_t(double(max_rows) * (8.0 / 33 + 8.0 / 1025)) +
                           (out_sa && !sa_dev ? uint64_t(max_rows) * 8 : 0);
     split = need <= avail;
   }
 
   // ---- workspace ---------------------------------------------------------
-  const uint64_t rows0 = split ? pl.N : uint64_t(max_rows);
+  uint64_t rows0 = uint64_t(max_rows);
+  if (split) {
+    uint64_t at = 0;
+    for (Slice& sl : slices) {
+      sl.arr0 = at;
+      at = (at + sl.rows + 3) & ~uint64_t(3);
+    }
+    rows0 = at;
+  }
   CX_TRY(ensure(c, c->vals[0], rows0 * pl.idb, "suffix ids"));
   CX_TRY(ensure(c, c->vals[1], uint64_t(max_rows) * pl.idb, "suffix ids"));
   CX_TRY(ensure(c, c->keys[0], rows0 * 4, "keys"));
@@ -790,8 +799,8 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
     if (split) {
       // The slice's part of the listed rows, and the spare array to sort into.
       sl.pregen = true;
-      r.vals[0] = vptr(c->vals[0].p, pl.idb, sl.row0);
-      r.keys[0] = static_cast<uint32_t*>(c->keys[0].p) + sl.row0;
+      r.vals[0] = vptr(c->vals[0].p, pl.idb, sl.arr0);
+      r.keys[0] = static_cast<uint32_t*>(c->keys[0].p) + sl.arr0;
     }
     CX_TRY(sort_slice(c, r, sl, &cur, tev));
     if (tev) CX_CUDA(c, cudaEventRecord(tev[2], st));

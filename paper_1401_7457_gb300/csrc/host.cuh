@@ -200,6 +200,8 @@ struct Slice {
   uint64_t row0 = 0;          // global BWT row of its first suffix
   bool pregen = false;        // its ids and first windows are already listed, in (length, read) order, in
                               // r.vals[0] / r.keys[0] (the split pass of a build in several slices)
+  uint64_t arr0 = 0;          // split pass: its first row in the listing arrays (a multiple of 4, so
+                              //   that its keys and ids start on 16-byte boundaries)
 };
 
 // A bucket-range part of a build (Section 3.3): only the suffixes whose first

@@ -68,6 +68,7 @@ struct PassArgs {
   uint32_t n_coll;
   uint32_t stall_tile0;              // test hook: tile 0 publishes nothing (its successor's wait runs out)
   uint64_t timeout_ns;               // look-back wait limit
+  uint32_t prefetch;                 // host: carried passes may prefetch into L2; kernel: tiles ahead (0 = none)
   // kSrcInitSplit: slice of every 4-base bucket (first window >> 24), and
   // each slice's outputs and rows.
   const uint8_t* split_of;

@@ -32,6 +32,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <type_traits>
 
@@ -59,6 +60,12 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t x, uint32_
       if (w < warp) warp_prefix += scratch[w];
   }
   return warp_prefix + incl - x;
+}
+
+// Asks the bulk-copy engine to bring `bytes` (a multiple of 16, 16-byte
+// aligned) of this GPU's memory into L2; nothing waits for it.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 template <class V, int THREADS, int IPT, int MIN_BLOCKS, int MODE, bool WRITE_KEY, bool FILTER>
@@ -105,6 +112,16 @@ __global__ void __launch_bounds__(THREADS, MIN_BLOCKS) k_onesweep(const PassArgs
   }
   __syncthreads();
   const uint32_t tile = s_tile;
+  if (CARRY_KEY && a.prefetch && tid == 0) {
+    // Tiles are taken in order, about one resident grid at a time: the tile
+    // that the CTA starting one grid later takes is read from HBM into L2
+    // now, so that its loads wait on L2 instead of HBM (whole tiles only).
+    const uint64_t ahead = uint64_t(tile) + a.prefetch;
+    if (ahead + 1 < a.n_tiles) {
+      prefetch_l2(a.keys_in + ahead * TILE, uint32_t(TILE) * 4u);
+      prefetch_l2(vals_in + ahead * TILE, uint32_t(TILE) * uint32_t(sizeof(V)));
+    }
+  }
   const I tile_base = I(tile) * I(TILE);
   const I warp_base = tile_base + I(warp) * 32u * IPT + lane;
   const I n_in = I(a.n_gen);
@@ -435,19 +452,32 @@ cudaError_t launch_mode(const PassArgs& a, cudaStream_t st) {
   auto kern = k_onesweep<V, S::threads, S::ipt, S::min_blocks, MODE, WK, F>;
   // Attributes are set once per instantiation and device (a bit per device;
   // threads that race here both set the same values).
-  static std::atomic<unsigned long long> configured{0};
+  // CTAs resident on the whole GPU, per device (set with the attributes, once;
+  // threads that race here store the same values).
+  static std::atomic<uint32_t> resident[64];
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  const unsigned long long bit = 1ull << (dev & 63);
-  if (!(configured.load(std::memory_order_acquire) & bit)) {
+  uint32_t grid_resident = resident[dev & 63].load(std::memory_order_acquire);
+  if (grid_resident == 0) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
-    configured.fetch_or(bit, std::memory_order_release);
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::threads, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    grid_resident = uint32_t(std::max(per_sm, 1) * std::max(sms, 1));
+    resident[dev & 63].store(grid_resident, std::memory_order_release);
   }
-  kern<<<a.n_tiles, S::threads, smem, st>>>(a);
+  PassArgs b = a;
+  b.prefetch = 0;
+  if (MODE == kSrcCarried && a.prefetch && (reinterpret_cast<uintptr_t>(a.keys_in) & 15u) == 0 &&
+      (reinterpret_cast<uintptr_t>(a.vals_in) & 15u) == 0)
+    b.prefetch = grid_resident;
+  kern<<<a.n_tiles, S::threads, smem, st>>>(b);
   return cudaGetLastError();
 }
 

@@ -156,6 +156,24 @@ def test_tile_shapes_identical(tile_items):
         assert_same(gpu_bwt(c, codes, lens), ref)
 
 
+@pytest.mark.parametrize("flags", [0, 1, 16, 17])
+@pytest.mark.parametrize("tile_items", [2048, 4096])
+def test_prefetching_carried_pass(flags, tile_items):
+    """The carried-key digit passes with the tile one resident grid ahead
+    read into L2 (the default) and without (plan flag 16): 32- and 64-bit ids
+    (plan flag 1), tiles of 2048 (64-bit ids only) and 4096 items, a ragged
+    last tile (1,246,845 suffixes), the group plan and the LSD plan (which
+    carries every window: 18 of its 25 passes); all equal the oracle."""
+    from paper_1401_7457_gb300 import binding
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    codes, lens = synth.sample_reads(synth.random_genome(60_000, 91), 12_345, 100, 92, 0.01)
+    ref = oracle_of(codes, lens)
+    for algorithm in (1, 2):
+        with binding.Context(device=0, algorithm=algorithm, plan_flags=flags, tile_items=tile_items) as c:
+            assert_same(gpu_bwt(c, codes, lens, want_sa=True), ref, sa=True)
+
+
 PLAN_CASES = ["uniform", "genome", "mixed", "all_a", "identical_cta", "identical_big", "two_letters", "short"]
 
 
