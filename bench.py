@@ -464,7 +464,8 @@ def run_batch_bench(args, rank, world):
     ctx.close()
     chosen = {}
     for (L, cls), t in sorted(picks.items()):
-        k = f"tile {t['tile_items']}, {'groups' if t['algorithm'] == 2 else 'lsd'}"
+        plan = f"groups l={t['prefix_len']}" if t['algorithm'] == 2 else "lsd"
+        k = f"tile {t['tile_items']}, {plan}"
         chosen[k] = chosen.get(k, 0) + 1
     line = {"metric": METRIC, "value": bases / out["batched"] / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": out["batched"] * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -729,7 +730,7 @@ def run_parts_bench(args, rank, world):
     w = torch.from_numpy(binding.pack_codes(codes).view(np.int32)).to(dev)
     ln = torch.from_numpy(lens.view(np.int32)).to(dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    ctx = binding.Context(device=0)
+    ctx = binding.Context(device=0, plan_flags=args.plan_flags)
     outs = ctx.build(w, ln)
     whole_ms = _timed(lambda: ctx.build(w, ln, *outs), args.steps, flush)
     counts = ctx.bucket_counts(w, ln)
@@ -794,7 +795,7 @@ def run_sharded_bench(args, rank, world):
     d_words = torch.from_numpy(words.view(np.int32)).to(dev)
     d_lens = torch.from_numpy(lens.view(np.int32)).to(dev)
     stream = torch.cuda.current_stream(dev)
-    ctx = binding.Context(device=local, budget_bytes=int(args.budget_gb * (1 << 30)))
+    ctx = binding.Context(device=local, budget_bytes=int(args.budget_gb * (1 << 30)), plan_flags=args.plan_flags)
     counts = ctx.bucket_counts(d_words, d_lens, stream=stream)
     plan = parts.plan_parts(counts, world)
     mine = plan[rank]
@@ -869,6 +870,8 @@ def main():
                     help="items per radix tile of the benchmark's contexts (0: the library's choice)")
     ap.add_argument("--plan-flags", type=int, default=0,
                     help="CXBWT_PLAN_* bits of the benchmark's contexts (1: 64-bit ids; for profiling captures)")
+    ap.add_argument("--prefix-len", type=int, default=0,
+                    help="l of the group plan of the benchmark's contexts (12 or 16; 0: the library's choice)")
     ap.add_argument("--budget-gb", type=float, default=0.0,
                     help="device budget of the library context (0: 90%% of free memory)")
     args = ap.parse_args()
@@ -970,7 +973,7 @@ def measure(args, dist, world, local, dev, desc, codes, lens, steps, e2e_steps):
     stream = torch.cuda.current_stream(dev)
 
     ctx = binding.Context(device=local, timing=True, budget_bytes=budget, plan_flags=args.plan_flags,
-                          tile_items=args.tile_items)
+                          tile_items=args.tile_items, prefix_len=args.prefix_len)
 
     def step():
         ctx.build(d_words, d_lens, d_bwt, d_dpos, d_cnt, stream=stream)
@@ -1027,7 +1030,8 @@ def measure(args, dist, world, local, dev, desc, codes, lens, steps, e2e_steps):
     h_bwt = torch.empty(n_words, dtype=torch.int32).pin_memory()
     h_dpos = torch.empty(n, dtype=torch.int64).pin_memory()
     h_cnt = torch.zeros(5, dtype=torch.int64).pin_memory()
-    ctx2 = binding.Context(device=local, budget_bytes=budget, plan_flags=args.plan_flags, tile_items=args.tile_items)
+    ctx2 = binding.Context(device=local, budget_bytes=budget, plan_flags=args.plan_flags, tile_items=args.tile_items,
+                           prefix_len=args.prefix_len)
     for _ in range(2):
         ctx2.build(h_words, h_lens, h_bwt, h_dpos, h_cnt, stream=stream)
     ctx2.reset_stats()

@@ -56,7 +56,7 @@
 extern "C" {
 #endif
 
-#define CXBWT_ABI_VERSION 2
+#define CXBWT_ABI_VERSION 3
 
 typedef enum {
   CXBWT_OK = 0,
@@ -75,9 +75,12 @@ typedef struct cxbwt_ctx cxbwt_ctx;
 typedef struct {
   uint64_t device_budget_bytes; /* cap on device memory the context may hold; 0 = 90% of free memory */
   int device;                   /* CUDA device ordinal */
-  int prefix_len;               /* l of the bucket plan (Section 3.1): must be 0, the planner chooses it
-                                   (4- or 8-base buckets for slices and parts, 16 bases for the group plan);
-                                   any other value gives CXBWT_EUNSUPPORTED */
+  int prefix_len;               /* l of the group plan (Section 3.1: suffixes sharing their first l bases
+                                   form one partition): its LSD passes sort the first l bases and each
+                                   partition is finished on chip.  0 = automatic (the autotuned value for
+                                   the build's size class, else 16), 12 or 16; other values give
+                                   CXBWT_EUNSUPPORTED.  Slices and parts are planned from buckets of 4 or
+                                   8 bases (16 when refined) whatever l is */
   int digit_bits;               /* radix digit width; 8 is the only width built (0 = 8, others give
                                    CXBWT_EUNSUPPORTED) */
   int tile_items;               /* items per radix tile: 0 = automatic (4096); 4096 or 8192 with 32-bit
@@ -119,9 +122,9 @@ typedef struct {
  *  AUTO     - GROUPS when the reads are at most 528 bases, else LSD.
  *  LSD      - stable LSD radix passes over every 4-base digit of the
  *             A-padded suffixes (Section 3.2 as stated: one pass per digit).
- *  GROUPS   - LSD passes over the first 16 bases only (the l-prefix
- *             partition of Section 3.1 with l = 16), then each group of
- *             suffixes sharing those bases is finished on chip. */
+ *  GROUPS   - LSD passes over the first l = 16 (or prefix_len = 12)
+ *             bases only (the l-prefix partition of Section 3.1), then each
+ *             group of suffixes sharing those bases is finished on chip. */
 #define CXBWT_ALGO_AUTO 0
 #define CXBWT_ALGO_LSD 1
 #define CXBWT_ALGO_GROUPS 2
@@ -339,17 +342,19 @@ int cxbwt_server_counters(cxbwt_server* s, uint64_t* completed, uint64_t* packs,
  * Times every candidate plan on one collection (device or host buffers) and
  * keeps the fastest in the context for builds of the same maximum read
  * length and size class (N within a factor of two) whose options leave
- * tile_items and algorithm automatic.  Candidates: tiles of 4096 or 8192
- * items (2048, 3072 or 4096 when the build carries 64-bit suffix ids) x the
- * group plan (reads of at most 528 bases) or the LSD plan.  The
- * radix digit is 8 bits (the only width built).  scratch_bwt (ceil(N / 16)
- * words) and scratch_dollar_pos (n_reads, may be NULL) receive the BWT;
- * every candidate produces the same one. */
+ * tile_items, algorithm and prefix_len automatic.  Candidates: tiles of
+ * 4096 or 8192 items (2048, 3072 or 4096 when the build carries 64-bit
+ * suffix ids) x the group plan with l = 16 (reads of at most 528 bases) or
+ * l = 12 (at most 524), or the LSD plan.  The radix digit is 8 bits (the
+ * only width built).  scratch_bwt (ceil(N / 16) words) and
+ * scratch_dollar_pos (n_reads, may be NULL) receive the BWT; every candidate
+ * produces the same one. */
 typedef struct {
   int tile_items;
   int algorithm;   /* CXBWT_ALGO_GROUPS or CXBWT_ALGO_LSD */
   int digit_bits;
   float best_ms;   /* device time of one build with the chosen plan */
+  int prefix_len;  /* l of the chosen group plan (12 or 16); 0 for the LSD plan */
 } cxbwt_tuning;
 int cxbwt_autotune(cxbwt_ctx* ctx, const uint32_t* reads_2bit, uint64_t n_reads, const uint32_t* lens,
                    uint32_t* scratch_bwt, uint64_t* scratch_dollar_pos, void* stream, cxbwt_tuning* out);

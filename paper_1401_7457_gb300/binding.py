@@ -93,7 +93,7 @@ SIGNATURES = {
 
 class Tuning(ctypes.Structure):
     _fields_ = [("tile_items", ctypes.c_int), ("algorithm", ctypes.c_int), ("digit_bits", ctypes.c_int),
-                ("best_ms", ctypes.c_float)]
+                ("best_ms", ctypes.c_float), ("prefix_len", ctypes.c_int)]
 
 
 class ServerOptions(ctypes.Structure):
@@ -338,7 +338,7 @@ class Context:
 
     def __init__(self, device: int = 0, budget_bytes: int = 0, async_: bool = False, timing: bool = False,
                  tile_items: int = 0, algorithm: int = 0, plan_flags: int = 0, batch_workers: int = 0,
-                 batch_small_mrows: int = 0, wait_limit_ms: int = 0):
+                 batch_small_mrows: int = 0, wait_limit_ms: int = 0, prefix_len: int = 0):
         L = lib()
         opt = Options()
         L.cxbwt_default_options(ctypes.byref(opt))
@@ -352,6 +352,7 @@ class Context:
         opt.batch_workers = batch_workers
         opt.batch_small_mrows = batch_small_mrows
         opt.wait_limit_ms = wait_limit_ms
+        opt.prefix_len = prefix_len
         h = ctypes.c_void_p()
         st = L.cxbwt_create(ctypes.byref(h), ctypes.byref(opt))
         if st != 0:
@@ -502,7 +503,7 @@ class Context:
         _check(lib().cxbwt_autotune(self._h, _ptr(reads_2bit), n, _ptr(lens), _ptr(scratch_bwt),
                                     _ptr(scratch_dollar_pos), _stream_ptr(stream), ctypes.byref(t)), self._h)
         return {"tile_items": t.tile_items, "algorithm": t.algorithm, "digit_bits": t.digit_bits,
-                "best_ms": t.best_ms}
+                "best_ms": t.best_ms, "prefix_len": t.prefix_len}
 
     def sync(self):
         _check(lib().cxbwt_sync(self._h), self._h)

@@ -169,8 +169,11 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
     first = false;
   }
   for (int64_t w = int64_t(pl.w_last); w >= 0; --w) {
+    // The group plan sorts the first l = depth bases of window 0 (4 bases per
+    // digit): 4 passes for l = 16, 3 for l = 12.
+    const uint32_t w_digits = (pl.groups && w == 0) ? pl.depth / 4 : 4u;
     const uint32_t d_lo = uint32_t(4 * w);
-    const uint32_t d_hi = std::min<uint32_t>(d_lo + 3, pl.D - 1);
+    const uint32_t d_hi = std::min<uint32_t>(d_lo + w_digits - 1, pl.D - 1);
     for (int64_t d = d_hi; d >= int64_t(d_lo); --d) {
       const bool first_in_window = (uint32_t(d) == d_hi);
       const bool last_in_window = (uint32_t(d) == d_lo);
@@ -208,8 +211,8 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
   }
   if (tev) CX_CUDA(c, cudaEventRecord(tev[1], st));
 
-  // ---- group plan: finish every group of equal first windows on chip ---------
-  if (pl.groups && pl.Lmax > 16) {
+  // ---- group plan: finish every group of equal first l bases on chip --------
+  if (pl.groups && pl.Lmax > pl.depth) {
     const uint64_t cta_cap = cta_list_cap(sl.rows), big_cap = big_list_cap(sl.rows, pl.seg_words);
     CX_CUDA(c, cudaMemsetAsync(r.d_seg, 0, 32, st));
     SegArgs g{};
@@ -217,7 +220,8 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
     g.vals = r.vals[cur];
     g.n_items = sl.rows;
     g.R = r.R;
-    g.depth = 16;
+    g.depth = pl.depth;
+    g.key_mask = depth_mask(pl.depth);
     g.cta_list = static_cast<uint2*>(c->seglist.p);
     g.cta_cap = uint32_t(cta_cap);
     g.big_list = g.cta_list + cta_cap;
@@ -227,7 +231,7 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
     CX_CUDA(c, launch_segsort(g, pl.seg_words, idb, c->sm_count, pl.n_words * 4 > (64u << 20), st));
     r.launches += 2;
     // Remainders too large for one CTA (rare: long runs of equal bases) are
-    // finished here with LSD passes over bases 16.. restricted to their rows.
+    // finished here with LSD passes over bases l.. restricted to their rows.
     CX_CUDA(c, cudaMemcpyAsync(c->h_small + 5, r.d_seg, 16, cudaMemcpyDeviceToHost, st));
     CX_CUDA(c, cudaStreamSynchronize(st));
     const uint32_t n_big = std::min<uint32_t>(reinterpret_cast<const uint32_t*>(c->h_small + 5)[1], g.big_cap);
@@ -239,12 +243,13 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
       CX_CUDA(c, cudaMemcpyAsync(big.data(), g.big_list, n_big * 8, cudaMemcpyDeviceToHost, st));
       CX_CUDA(c, cudaStreamSynchronize(st));
       r.d2h += n_big * 8;
-      const uint32_t n_win = pl.W - 1;
+      // Windows of bases [l + 16u, l + 16u + 16), u < n_win, cover bases l .. Lmax-1.
+      const uint32_t n_win = (pl.Lmax - pl.depth + 15) / 16;
       auto* rh = static_cast<uint32_t*>(c->rhist.p);
       for (const uint2& bg : big) {
         const uint32_t s0 = bg.x, m = bg.y;
         CX_CUDA(c, cudaMemsetAsync(rh, 0, size_t(n_win) * 4 * kRadix * 4, st));
-        CX_CUDA(c, launch_range_hist(vptr(r.vals[cur], idb, s0), idb, m, r.R, n_win, rh, c->sm_count, st));
+        CX_CUDA(c, launch_range_hist(vptr(r.vals[cur], idb, s0), idb, m, r.R, pl.depth, n_win, rh, c->sm_count, st));
         r.launches += 2;
         void* gv[2] = {vptr(r.vals[cur], idb, s0), vptr(r.vals[cur ^ 1], idb, s0)};
         uint32_t* gk[2] = {r.keys[0] + s0, r.keys[1] + s0};
@@ -253,12 +258,12 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
         b.n_gen = m;
         b.n_out = m;
         b.n_tiles = uint32_t((m + TILE - 1) / TILE);
-        for (uint32_t w = pl.W - 1; w >= 1; --w) {
-          const uint32_t d_lo = 4 * w;
-          const uint32_t d_hi = std::min<uint32_t>(d_lo + 3, pl.D - 1);
-          for (int64_t d = d_hi; d >= int64_t(d_lo); --d) {
-            const bool first_in_window = (uint32_t(d) == d_hi);
-            const bool last_in_window = (uint32_t(d) == d_lo);
+        for (uint32_t u = n_win; u-- > 0;) {
+          const uint32_t c0 = pl.depth + 16 * u;
+          const uint32_t n_dig = std::min<uint32_t>(4, (pl.Lmax - c0 + 3) / 4);  // digits holding bases < Lmax
+          for (int64_t j = int64_t(n_dig) - 1; j >= 0; --j) {
+            const bool first_in_window = (uint32_t(j) == n_dig - 1);
+            const bool last_in_window = (j == 0);
             const int mode = first_in_window ? kSrcExtract : kSrcCarried;
             const bool write_key = !last_in_window;
             b.vals_in = gv[gc];
@@ -266,9 +271,9 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
             b.keys_in = (mode == kSrcCarried) ? gk[gki] : nullptr;
             const int kout = (mode == kSrcCarried) ? (gki ^ 1) : gki;
             b.keys_out = write_key ? gk[kout] : nullptr;
-            b.digit_base = rh + size_t((w - 1) * 4 + (uint32_t(d) - d_lo)) * kRadix;
-            b.key_shift = 24u - 8u * (uint32_t(d) - d_lo);
-            b.window_c0 = 16 * w;
+            b.digit_base = rh + size_t(u * 4 + uint32_t(j)) * kRadix;
+            b.key_shift = 24u - 8u * uint32_t(j);
+            b.window_c0 = c0;
             b.epoch = ++c->epoch;
             CX_CUDA(c, launch_onesweep(b, mode, write_key, false, idb, r.shape, st));
             gc ^= 1;
@@ -427,19 +432,23 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   pl.W = (pl.Lmax + 15) / 16;
   pl.len_passes = pl.uniform ? 0 : (pl.Lmax > 255 ? 2 : 1);
   pl.n_words = (sum + 15) / 16;
-  pl.seg_words = segsort_words(pl.Lmax);
-  int algorithm = c->opt.algorithm, tile_items = c->opt.tile_items;
+  int algorithm = c->opt.algorithm, tile_items = c->opt.tile_items, depth = c->opt.prefix_len;
   {
-    int t_tile = 0, t_algo = 0;
-    if (tuned_choice(c, pl.Lmax, pl.N, &t_tile, &t_algo)) {
+    int t_tile = 0, t_algo = 0, t_depth = 0;
+    if (tuned_choice(c, pl.Lmax, pl.N, &t_tile, &t_algo, &t_depth)) {
       if (algorithm == CXBWT_ALGO_AUTO) algorithm = t_algo;
       if (tile_items == 0) tile_items = t_tile;
+      if (depth == 0) depth = t_depth;
     }
   }
+  pl.depth = depth ? uint32_t(depth) : 16u;
+  pl.seg_words = segsort_words(pl.Lmax, pl.depth);
   switch (algorithm) {
     case CXBWT_ALGO_LSD: pl.groups = false; break;
     case CXBWT_ALGO_GROUPS:
-      if (!pl.seg_words) return fail(c, CXBWT_EUNSUPPORTED, "the group plan handles reads of at most 528 bases");
+      if (!pl.seg_words)
+        return fail(c, CXBWT_EUNSUPPORTED, "the group plan handles reads of at most %u bases with l = %u",
+                    pl.depth + 512, pl.depth);
       pl.groups = true;
       break;
     case CXBWT_ALGO_AUTO: pl.groups = pl.seg_words != 0; break;
@@ -752,7 +761,7 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   const uint32_t split_row = std::max<uint32_t>(pl.D + pl.len_passes, 5);
   CX_TRY(ensure(c, c->base, uint64_t(split_row + 2) * kRadix * 4, "digit bases"));
   if (pl.uniform && !c->lenhist.p) CX_TRY(ensure(c, c->lenhist, 4, "length histogram"));
-  if (pl.groups && pl.Lmax > 16) {
+  if (pl.groups && pl.Lmax > pl.depth) {
     CX_TRY(ensure(c, c->seglist, (cta_list_cap(max_rows) + big_list_cap(max_rows, pl.seg_words)) * 8, "group lists"));
     CX_TRY(ensure(c, c->rhist, size_t(pl.W) * 4 * kRadix * 4, "group digit counts"));
   }
@@ -990,8 +999,8 @@ int cxbwt_create(cxbwt_ctx** out, const cxbwt_options* opt) {
     g_create_error = "digit_bits: only 8-bit digits are built";
     return CXBWT_EUNSUPPORTED;
   }
-  if (o.prefix_len != 0) {
-    g_create_error = "prefix_len: the planner chooses the bucket prefix itself (leave it 0)";
+  if (o.prefix_len != 0 && o.prefix_len != 12 && o.prefix_len != 16) {
+    g_create_error = "prefix_len: the group plan sorts the first 12 or 16 bases (0 = automatic)";
     return CXBWT_EUNSUPPORTED;
   }
   int ndev = 0;

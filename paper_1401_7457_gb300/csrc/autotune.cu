@@ -1,14 +1,19 @@
-// cxbwt_autotune: choose the tile shape and sort plan by timing them.
+// cxbwt_autotune: choose the tile shape, the sort plan and the group plan's
+// depth by timing them.
 //
 // For one collection (device memory), every candidate (tile of 4096 or 8192
 // items with 32-bit suffix ids, of 2048, 3072 or 4096 with 64-bit ones;
-// group plan or LSD plan where both apply) is built twice and timed
-// with CUDA events on the caller's stream; the fastest choice is kept in the
-// context for builds of the same maximum read length and size class (N
-// within a factor of two).  Builds whose options leave the tile and the plan
-// automatic then use it.  Every candidate gives the same BWT; only speed
-// differs.  The radix digit width is fixed at 8 bits (the only width built),
-// and the first-window depth of the group plan at 16 bases.
+// the group plan with its first l = 16 or l = 12 bases sorted by LSD passes
+// (four or three passes, then groups sharing those bases finished on chip),
+// or the LSD plan, where they apply) is built three times and the last two
+// are timed with CUDA events on the caller's stream; the fastest choice is
+// kept in the context for builds of the same maximum read length and size
+// class (N within a factor of two).  Builds whose options leave the tile,
+// the plan and prefix_len automatic then use it.  Every candidate gives the
+// same BWT; only speed differs: a smaller l saves a pass over every suffix
+// and leaves larger groups to finish, which pays when the collection's
+// l-prefixes are still rare (reads of a small genome).  The radix digit
+// width is fixed at 8 bits (the only width built).
 #include <cuda_runtime.h>
 
 #include "host.cuh"
@@ -46,21 +51,24 @@ extern "C" int cxbwt_autotune(cxbwt_ctx* c, const uint32_t* reads_2bit, uint64_t
   const cxbwt_options saved = c->opt;
   const auto saved_tuned = c->tuned;
   c->tuned.clear();
-  struct Cand { int tile, algo; };
+  struct Cand { int tile, algo, depth; };
   std::vector<Cand> cands;
   const std::vector<int> tiles = probe.idb == 8 ? std::vector<int>{2048, 3072, 4096} : std::vector<int>{4096, 8192};
-  for (int algo : {CXBWT_ALGO_GROUPS, CXBWT_ALGO_LSD})
-    for (int t : tiles) cands.push_back(Cand{t, algo});
+  for (int t : tiles) {
+    if (segsort_words(Lmax, 16)) cands.push_back(Cand{t, CXBWT_ALGO_GROUPS, 16});
+    if (segsort_words(Lmax, 12) && Lmax > 12) cands.push_back(Cand{t, CXBWT_ALGO_GROUPS, 12});
+    cands.push_back(Cand{t, CXBWT_ALGO_LSD, 0});
+  }
   cudaEvent_t e0, e1;
   CX_CUDA(c, cudaEventCreate(&e0));
   CX_CUDA(c, cudaEventCreate(&e1));
   float best = -1.f;
-  Cand pick{0, 0};
+  Cand pick{0, 0, 0};
   int status = CXBWT_OK;
   for (const Cand& cd : cands) {
-    if (cd.algo == CXBWT_ALGO_GROUPS && !segsort_words(Lmax)) continue;
     c->opt.tile_items = cd.tile;
     c->opt.algorithm = cd.algo;
+    c->opt.prefix_len = cd.depth;
     c->opt.async = 0;
     float ms_best = 1e30f;
     int st_c = CXBWT_OK;
@@ -91,16 +99,17 @@ extern "C" int cxbwt_autotune(cxbwt_ctx* c, const uint32_t* reads_2bit, uint64_t
   const uint64_t key = tune_key(Lmax, N);
   bool found = false;
   for (auto& e : c->tuned)
-    if (e.first == key) {
-      e.second = {pick.tile, pick.algo};
+    if (e.key == key) {
+      e = TunedPlan{key, pick.tile, pick.algo, pick.depth};
       found = true;
     }
-  if (!found) c->tuned.push_back({key, {pick.tile, pick.algo}});
+  if (!found) c->tuned.push_back(TunedPlan{key, pick.tile, pick.algo, pick.depth});
   if (out) {
     out->tile_items = pick.tile;
     out->algorithm = pick.algo;
     out->digit_bits = 8;
     out->best_ms = best;
+    out->prefix_len = pick.depth;
   }
   return CXBWT_OK;
 }

@@ -81,7 +81,20 @@ int build_pack(cxbwt_ctx* c, const cxbwt_collection* colls, const std::vector<ui
   pl.W = (L + 15) / 16;
   pl.len_passes = 0;
   pl.n_words = words;
-  pl.seg_words = segsort_words(L);
+  // The group plan's depth l: the option, else the autotuned one for the
+  // pack's size class, else 16 (16 also when l = 12 leaves too many bases).
+  int depth = c->opt.prefix_len;
+  {
+    int t_tile = 0, t_algo = 0, t_depth = 0;
+    if (!depth && tuned_choice(c, L, pl.N, &t_tile, &t_algo, &t_depth) && t_algo == CXBWT_ALGO_GROUPS)
+      depth = t_depth;
+  }
+  pl.depth = depth ? uint32_t(depth) : 16u;
+  pl.seg_words = segsort_words(L, pl.depth);
+  if (!pl.seg_words) {
+    pl.depth = 16;
+    pl.seg_words = segsort_words(L, 16);
+  }
   pl.groups = true;
   pl.w_last = 0;
   plan_ids(pl, (c->opt.plan_flags & CXBWT_PLAN_ID64) != 0, (c->opt.plan_flags & CXBWT_PLAN_CARRY_BASE) != 0);
@@ -417,7 +430,7 @@ extern "C" int cxbwt_build_batch(cxbwt_ctx* c, const cxbwt_collection* colls, ui
   std::vector<int64_t> open(65536, -1);
   for (uint32_t i = 0; i < k; ++i) {
     const Coll& ci = info[i];
-    if (!ci.uniform || !segsort_words(ci.L) || ci.N > small) {
+    if (!ci.uniform || !segsort_words(ci.L, 16) || ci.N > small) {
       Item it;
       it.colls.push_back(i);
       it.rows = ci.N;

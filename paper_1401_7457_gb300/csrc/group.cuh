@@ -22,11 +22,12 @@ constexpr uint64_t cta_list_cap(uint64_t rows) { return rows / 33 + 1; }
 constexpr uint64_t big_list_cap(uint64_t rows, int nw) { return rows / (uint64_t(cta_rows_for(nw)) + 1) + 1; }
 
 struct SegArgs {
-  const uint32_t* keys;   // first 16-base window of each row, ascending
+  const uint32_t* keys;   // first 16-base window of each row; ascending under key_mask
   void* vals;             // suffix ids (uint32 or uint64), sorted by that window; finished in place
   uint32_t n_items;
   ReadIndex R;
-  uint32_t depth;         // bases already sorted (16)
+  uint32_t depth;         // bases already sorted: l of the group plan (12 or 16)
+  uint32_t key_mask;      // the window bits of those bases: rows are in one group when their masked keys are equal
   uint2* cta_list;        // (first row, rows) of remainders of 33 .. kCtaMax rows
   uint32_t cta_cap;
   uint2* big_list;        // remainders of more rows, finished by the host
@@ -37,13 +38,17 @@ struct SegArgs {
 };
 
 // Key words a group remainder is sorted by for reads of at most max_len bases
-// (a compiled width >= ceil((max_len - 16) / 16)), or 0 if too long.
-int segsort_words(uint32_t max_len);
+// when the first `depth` bases are sorted already (a compiled width >=
+// ceil((max_len - depth) / 16)), or 0 if too long.
+int segsort_words(uint32_t max_len, uint32_t depth);
+// The bits of a 16-base window that hold its first `depth` bases.
+constexpr uint32_t depth_mask(uint32_t depth) { return depth >= 16 ? 0xFFFFFFFFu : ~(0xFFFFFFFFu >> (2u * depth)); }
 // wide: warp windows of 64 rows (two per lane) instead of 32, for read
 // stores out of L2.
 cudaError_t launch_segsort(const SegArgs& a, int nw, int id_bytes, int sm_count, bool wide, cudaStream_t st);
-// Digit bases (exclusive, per digit position) of windows 1 .. n_win over n rows of vals.
-cudaError_t launch_range_hist(const void* vals, int id_bytes, uint32_t n, const ReadIndex& R, uint32_t n_win,
-                              uint32_t* hist, int sm_count, cudaStream_t st);
+// Digit bases (exclusive, per digit position) of the n_win windows of bases
+// [c0, c0 + 16), [c0 + 16, c0 + 32), ... over n rows of vals.
+cudaError_t launch_range_hist(const void* vals, int id_bytes, uint32_t n, const ReadIndex& R, uint32_t c0,
+                              uint32_t n_win, uint32_t* hist, int sm_count, cudaStream_t st);
 
 }  // namespace cxbwt

@@ -25,6 +25,13 @@ struct DevBuf {
 
 constexpr uint64_t kTimeoutNs = 1000000000ull;  // look-back waits give up after 1 s
 
+// An autotuned plan for builds of one maximum read length and size class
+// (key: tune_key): tile items, algorithm, and the group plan's depth l.
+struct TunedPlan {
+  uint64_t key;
+  int tile, algo, depth;
+};
+
 }  // namespace host
 }  // namespace cxbwt
 
@@ -48,9 +55,9 @@ struct cxbwt_ctx {
   cudaStream_t last_stream = nullptr;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   cxbwt_stats stats{};
-  // Autotuner choices (autotune.cu): key (max read length << 8 | log2 N class)
-  // -> (tile items, algorithm).  Used when the options leave them automatic.
-  std::vector<std::pair<uint64_t, std::pair<int, int>>> tuned;
+  // Autotuner choices (autotune.cu), one per maximum read length and size
+  // class.  Used when the options leave tile, algorithm and depth automatic.
+  std::vector<cxbwt::host::TunedPlan> tuned;
   void* batch_pool = nullptr;             // worker contexts of cxbwt_build_batch (batch.cu), created on first use
   void (*batch_pool_free)(void*) = nullptr;
 };
@@ -164,6 +171,7 @@ struct Plan {
   int idb = 4;            // suffix id bytes
   uint32_t sym = 0;       // id bits holding the preceding base (0 or 2)
   bool groups = false;
+  uint32_t depth = 16;    // group plan: bases sorted by the LSD passes (l of Section 3.1: 12 or 16)
   int seg_words = 0;
   uint32_t w_last = 0;    // windows [0, w_last] are sorted by LSD passes over all rows of a slice
 };
@@ -284,13 +292,15 @@ inline uint64_t tune_key(uint32_t max_len, uint64_t n_suffixes) {
   return (uint64_t(max_len) << 8) | cls;
 }
 
-// The autotuned (tile items, algorithm) of a build, or false.
-inline bool tuned_choice(const cxbwt_ctx* c, uint32_t max_len, uint64_t n_suffixes, int* tile, int* algo) {
+// The autotuned (tile items, algorithm, depth) of a build, or false.
+inline bool tuned_choice(const cxbwt_ctx* c, uint32_t max_len, uint64_t n_suffixes, int* tile, int* algo,
+                         int* depth) {
   const uint64_t k = tune_key(max_len, n_suffixes);
   for (const auto& e : c->tuned)
-    if (e.first == k) {
-      *tile = e.second.first;
-      *algo = e.second.second;
+    if (e.key == k) {
+      *tile = e.tile;
+      *algo = e.algo;
+      *depth = e.depth;
       return true;
     }
   return false;

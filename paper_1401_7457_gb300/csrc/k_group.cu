@@ -1,19 +1,21 @@
-// Finishing the sort inside groups of suffixes that share their first 16 bases.
+// Finishing the sort inside groups of suffixes that share their first l
+// bases (l = 16, or 12: the depth of the group plan).
 //
-// After the stable LSD passes over the first 16-base window, the suffix ids
-// are ordered by those 16 bases (A-padded) and, among equal windows, by
-// (suffix length, read): a "group" is a maximal run of equal windows.  This
-// is the partition step of Section 3.1 (suffixes with the same l-prefix form
-// one partition, l = 16 here) followed by sorting each partition; groups are
-// small for reads (about the coverage), so each one is finished on chip
-// instead of with more passes over HBM:
+// After the stable LSD passes over the first l bases of the 16-base window,
+// the suffix ids are ordered by those bases (A-padded) and, among equal
+// ones, by (suffix length, read): a "group" is a maximal run of rows whose
+// windows agree on their first l bases (keys equal under key_mask).  This is
+// the partition step of Section 3.1 (suffixes with the same l-prefix form
+// one partition) followed by sorting each partition; groups are small for
+// reads (about the coverage), so each one is finished on chip instead of
+// with more passes over HBM:
 //
-//   * the members of a group whose suffix has at most 16 bases are final:
-//     their whole A-padded key is the window, they tie with each other and
+//   * the members of a group whose suffix has at most l bases are final:
+//     their whole A-padded key is the prefix, they tie with each other and
 //     with every longer member's padded key only when that member continues
 //     with A's, and then the shorter one is smaller - the group is already in
 //     (length, read) order, so they form its prefix and stay where they are;
-//   * the rest of the group (the "remainder") is sorted by bases 16.. of the
+//   * the rest of the group (the "remainder") is sorted by bases l.. of the
 //     suffix, A-padded, ties kept in the current order (stable): by one warp
 //     when it has at most 64 members (32 for the widest keys) - each member
 //     counts the members that order before it -, by one CTA with a
@@ -257,16 +259,16 @@ __device__ uint32_t next_head(const SegArgs& a, uint32_t from, int lane) {
   if (from >= a.n_items) return a.n_items;
   for (uint32_t x = from;; x += 32) {
     const uint32_t y = x + lane;
-    const bool head = (y < a.n_items) && (y == 0 || a.keys[y] != a.keys[y - 1]);
+    const bool head = (y < a.n_items) && (y == 0 || ((a.keys[y] ^ a.keys[y - 1]) & a.key_mask) != 0u);
     const bool stop = head || y >= a.n_items;
     const uint32_t m = __ballot_sync(0xFFFFFFFFu, stop);
     if (m) return min(x + __ffs(m) - 1, a.n_items);
     if (x - from >= 64) {  // a long run of equal windows: binary search for its end
-      const uint32_t key = a.keys[x + 31];
+      const uint32_t key = a.keys[x + 31] & a.key_mask;
       uint32_t lo = x + 32, hi = a.n_items;
       while (lo < hi) {
         const uint32_t mid = lo + (hi - lo) / 2;
-        if (a.keys[mid] == key) lo = mid + 1; else hi = mid;
+        if ((a.keys[mid] & a.key_mask) == key) lo = mid + 1; else hi = mid;
       }
       return lo;
     }
@@ -330,7 +332,7 @@ __device__ __forceinline__ void segsort_warp_body(const SegArgs& a) {
 #pragma unroll
       for (int h = 0; h < SPAN / 32; ++h) {
         const uint32_t y = cur + 1 + lane + 32u * h;
-        const bool head = (y >= a.n_items) || (a.keys[y] != a.keys[y - 1]);
+        const bool head = (y >= a.n_items) || (((a.keys[y] ^ a.keys[y - 1]) & a.key_mask) != 0u);
         hm |= H(__ballot_sync(0xFFFFFFFFu, head)) << (32 * h);
         past |= H(__ballot_sync(0xFFFFFFFFu, head && y >= limit)) << (32 * h);
       }
@@ -442,11 +444,11 @@ __global__ void __launch_bounds__(THREADS) k_segsort_cta(const SegArgs a, const 
   }
 }
 
-// Digit counts of bases [16, 16 * (1 + NWIN)) over rows [0, n) of vals: the
+// Digit counts of bases [c0, c0 + 16 * n_win) over rows [0, n) of vals: the
 // per-pass histograms of the LSD passes that finish one big group.
-// hist[(w * 4 + j) * 256 + digit] for window w (bases 16(w+1) ..) and digit j.
+// hist[(w * 4 + j) * 256 + digit] for window w (bases c0 + 16w ..) and digit j.
 template <class V>
-__global__ void k_range_hist(const V* vals, uint32_t n, ReadIndex R, uint32_t n_win, uint32_t* hist) {
+__global__ void k_range_hist(const V* vals, uint32_t n, ReadIndex R, uint32_t c0, uint32_t n_win, uint32_t* hist) {
   extern __shared__ uint32_t sh[];
   const uint32_t bins = n_win * 4 * kRadix;
   for (uint32_t x = threadIdx.x; x < bins; x += blockDim.x) sh[x] = 0;
@@ -454,7 +456,7 @@ __global__ void k_range_hist(const V* vals, uint32_t n, ReadIndex R, uint32_t n_
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     const Suffix s = decode(R, vals[r]);
     for (uint32_t w = 0; w < n_win; ++w) {
-      const uint32_t key = window16(R, s, 16u * (w + 1));
+      const uint32_t key = window16(R, s, c0 + 16u * w);
 #pragma unroll
       for (int j = 0; j < 4; ++j) atomicAdd(&sh[(w * 4 + j) * kRadix + ((key >> (24 - 8 * j)) & 255u)], 1u);
     }
@@ -542,8 +544,8 @@ cudaError_t launch_v(const SegArgs& a, int nw, int sm_count, bool wide, cudaStre
 
 }  // namespace
 
-int segsort_words(uint32_t max_len) {
-  const uint32_t rest = max_len > 16 ? max_len - 16 : 0;  // bases after the first window
+int segsort_words(uint32_t max_len, uint32_t depth) {
+  const uint32_t rest = max_len > depth ? max_len - depth : 0;  // bases after the sorted ones
   const uint32_t nw = (rest + 15) / 16;
   if (nw <= 2) return 2;
   if (nw <= 4) return 4;
@@ -561,8 +563,8 @@ cudaError_t launch_segsort(const SegArgs& a, int nw, int id_bytes, int sm_count,
   return id_bytes == 8 ? launch_v<uint64_t>(a, nw, sm_count, wide, st) : launch_v<uint32_t>(a, nw, sm_count, wide, st);
 }
 
-cudaError_t launch_range_hist(const void* vals, int id_bytes, uint32_t n, const ReadIndex& R, uint32_t n_win,
-                              uint32_t* hist, int sm_count, cudaStream_t st) {
+cudaError_t launch_range_hist(const void* vals, int id_bytes, uint32_t n, const ReadIndex& R, uint32_t c0,
+                              uint32_t n_win, uint32_t* hist, int sm_count, cudaStream_t st) {
   if (n == 0 || n_win == 0) return cudaSuccess;
   const size_t smem = size_t(n_win) * 4 * kRadix * 4;
   uint32_t blocks = (n + 255) / 256;
@@ -571,11 +573,11 @@ cudaError_t launch_range_hist(const void* vals, int id_bytes, uint32_t n, const 
   if (id_bytes == 8) {
     e = cudaFuncSetAttribute(k_range_hist<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    k_range_hist<uint64_t><<<blocks, 256, smem, st>>>(static_cast<const uint64_t*>(vals), n, R, n_win, hist);
+    k_range_hist<uint64_t><<<blocks, 256, smem, st>>>(static_cast<const uint64_t*>(vals), n, R, c0, n_win, hist);
   } else {
     e = cudaFuncSetAttribute(k_range_hist<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    k_range_hist<uint32_t><<<blocks, 256, smem, st>>>(static_cast<const uint32_t*>(vals), n, R, n_win, hist);
+    k_range_hist<uint32_t><<<blocks, 256, smem, st>>>(static_cast<const uint32_t*>(vals), n, R, c0, n_win, hist);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -102,7 +102,7 @@ extern "C" int cxbwt_build_noalloc(const uint32_t* reads_2bit, uint64_t n_reads,
   const uint64_t N = sum + n_reads;
   // Sizes beyond what the static array holds are rejected before any device work.
   if (N > kMaxRows || L > kMaxLen) return CXBWT_EUNSUPPORTED;
-  const int seg_words = segsort_words(L);
+  const int seg_words = segsort_words(L, 16);
   if (!seg_words) return CXBWT_EUNSUPPORTED;
 
   int dev = 0;
@@ -197,6 +197,7 @@ extern "C" int cxbwt_build_noalloc(const uint32_t* reads_2bit, uint64_t n_reads,
     g.n_items = uint32_t(N);
     g.R = R;
     g.depth = 16;
+    g.key_mask = depth_mask(16);
     g.cta_list = reinterpret_cast<uint2*>(base + kOffSeg);
     g.cta_cap = uint32_t(kCtaCap);
     g.big_list = g.cta_list + kCtaCap;
@@ -215,7 +216,7 @@ extern "C" int cxbwt_build_noalloc(const uint32_t* reads_2bit, uint64_t n_reads,
       NA_CUDA(cudaStreamSynchronize(st));
       const uint32_t s0 = bg.x, m = bg.y, n_win = W - 1;
       NA_CUDA(cudaMemsetAsync(rh, 0, size_t(n_win) * 4 * kRadix * 4, st));
-      NA_CUDA(launch_range_hist(static_cast<uint32_t*>(vals[cur]) + s0, 4, m, R, n_win, rh, sm_count, st));
+      NA_CUDA(launch_range_hist(static_cast<uint32_t*>(vals[cur]) + s0, 4, m, R, 16, n_win, rh, sm_count, st));
       void* gv[2] = {static_cast<uint32_t*>(vals[cur]) + s0, static_cast<uint32_t*>(vals[cur ^ 1]) + s0};
       uint32_t* gk[2] = {keys[0] + s0, keys[1] + s0};
       int gc = 0, gki = 0;

@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version(lib):
-    assert lib.cxbwt_abi_version() == 2
+    assert lib.cxbwt_abi_version() == 3
 
 
 def test_pack_unpack_roundtrip(lib):
@@ -150,7 +150,7 @@ def test_binding_rejects_wrong_element_sizes():
 def test_create_rejects_options_it_does_not_build(lib):
     """Checked before any device work, so this runs without a GPU."""
     from paper_1401_7457_gb300 import binding
-    for field, value in (("prefix_len", 4), ("digit_bits", 4)):
+    for field, value in (("prefix_len", 4), ("prefix_len", 8), ("prefix_len", 20), ("digit_bits", 4)):
         opt = binding.Options()
         lib.cxbwt_default_options(ctypes.byref(opt))
         setattr(opt, field, value)
@@ -175,3 +175,20 @@ def test_no_cpu_fallback(lib, monkeypatch):
     monkeypatch.setattr(binding, "LIB_PATH", os.path.join(ROOT, "no_such_dir", "libcxbwt.so"))
     with pytest.raises(RuntimeError, match="not built"):
         binding.pack_codes(np.zeros(4, dtype=np.uint8))
+
+
+def test_create_accepts_group_depths_it_builds(lib):
+    """prefix_len 0, 12 and 16 pass the option check: without a GPU the call
+    then fails for want of a device (CXBWT_ECUDA), not for the option."""
+    import torch
+
+    from paper_1401_7457_gb300 import binding
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present: creation would succeed")
+    for value in (0, 12, 16):
+        opt = binding.Options()
+        lib.cxbwt_default_options(ctypes.byref(opt))
+        opt.prefix_len = value
+        h = ctypes.c_void_p()
+        assert lib.cxbwt_create(ctypes.byref(h), ctypes.byref(opt)) == -3
+        assert b"prefix_len" not in lib.cxbwt_last_error(None)

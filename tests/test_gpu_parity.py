@@ -214,6 +214,69 @@ def test_plans_identical(case, algorithm):
         assert_same(gpu_bwt(c, codes, lens, want_sa=True), ref, sa=True)
 
 
+@pytest.mark.parametrize("case", PLAN_CASES)
+def test_group_plan_depth_12(case):
+    """The group plan with l = 12 (prefix_len): three LSD passes sort the
+    first 12 bases and the groups sharing them are finished from base 12 on
+    (the warp and CTA finishes, and for all-A and identical reads the
+    big-group LSD passes over windows starting at base 12); the oracle's
+    result, suffix order included."""
+    from paper_1401_7457_gb300 import binding
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    codes, lens = plan_case(case)
+    with binding.Context(device=0, algorithm=2, prefix_len=12) as c:
+        assert_same(gpu_bwt(c, codes, lens, want_sa=True), oracle_of(codes, lens), sa=True)
+
+
+def test_group_plan_depth_12_read_lengths():
+    """Keys of 24 words (300-base reads, groups of 1,500 equal suffixes past
+    the CTA limit), reads of 524 bases (the longest l = 12 finishes on chip),
+    and 528-base reads, which l = 12 leaves to the LSD plan when the plan is
+    automatic and refuses when the group plan is asked for."""
+    from paper_1401_7457_gb300 import binding
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    one = np.random.default_rng(95).integers(0, 4, size=300).astype(np.uint8)
+    cases = [(np.tile(one, 1500), np.full(1500, 300, dtype=np.uint32))]
+    g = synth.random_genome(524 * 800 // 30, 96)
+    cases.append(synth.sample_reads(g, 800, 524, 97, 0.01))
+    for codes, lens in cases:
+        with binding.Context(device=0, algorithm=2, prefix_len=12) as c:
+            assert_same(gpu_bwt(c, codes, lens), oracle_of(codes, lens))
+    codes, lens = synth.uniform_reads(300, 528, 98)
+    with binding.Context(device=0, prefix_len=12) as c:
+        assert_same(gpu_bwt(c, codes, lens), oracle_of(codes, lens))
+    with binding.Context(device=0, algorithm=2, prefix_len=12) as c:
+        with pytest.raises(binding.CxbwtError) as e:
+            c.build(binding.pack_codes(codes), lens)
+        assert e.value.status == -5
+
+
+def test_group_plan_depth_12_batch():
+    """A batch whose small collections are packed and sorted as one with
+    l = 12; every collection's BWT is the oracle's."""
+    from paper_1401_7457_gb300 import binding
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    cols = []
+    for j in range(6):
+        g = synth.random_genome(20_000 + 5_000 * j, 110 + j)
+        cols.append(synth.sample_reads(g, 2_000 + 700 * j, (36, 76, 100)[j % 3], 120 + j, 0.01))
+    with binding.Context(device=0, prefix_len=12) as c:
+        outs = []
+        for codes, lens in cols:
+            n_sym = int(lens.sum()) + lens.size
+            outs.append((binding.pack_codes(codes), np.ascontiguousarray(lens, dtype=np.uint32),
+                         np.zeros((n_sym + 15) // 16, dtype=np.uint32), np.zeros(lens.size, dtype=np.uint64),
+                         np.zeros(5, dtype=np.uint64)))
+        c.build_batch(outs)
+    for (codes, lens), (_, _, bwt, dpos, cnt) in zip(cols, outs):
+        ref = oracle_of(codes, lens)
+        assert binding.unpack_ascii(bwt, dpos, len(ref["bwt"])) == ref["bwt"]
+        assert np.array_equal(dpos, ref["dollar_pos"]) and np.array_equal(cnt, ref["counts"])
+
+
 def test_group_plan_rejects_long_reads():
     from paper_1401_7457_gb300 import binding
     if not torch.cuda.is_available():
@@ -241,6 +304,7 @@ def test_autotune_then_build():
     with binding.Context(device=0) as c:
         t = c.autotune(words, dl, scratch)
         assert t["tile_items"] in (4096, 8192) and t["algorithm"] in (1, 2) and t["best_ms"] > 0
+        assert t["prefix_len"] == (0 if t["algorithm"] == 1 else t["prefix_len"]) and t["prefix_len"] in (0, 12, 16)
         assert_same(gpu_bwt(c, codes, lens), oracle_of(codes, lens))
         # same size class, other data
         codes2, lens2 = synth.uniform_reads(12_000, 100, 83)

@@ -175,3 +175,19 @@ def test_mixed_length_slices(lo, hi, flags):
     with binding.Context(device=0, budget_bytes=budget_for(N, 4, 8 if flags else 4), plan_flags=flags) as c:
         assert_same(gpu_bwt(c, codes, lens, want_sa=True), ref, sa=True)
         assert c.stats()["slices"] >= 3
+
+
+@pytest.mark.parametrize("flags", [0, 1 | 8])
+def test_group_depth_12_in_slices(genome_reads, flags):
+    """The group plan with l = 12 (three LSD passes, groups finished from
+    base 12 on) in a build of about three device-memory-bounded slices, with
+    32-bit ids and with 64-bit ids carrying the preceding base."""
+    _need_gpu()
+    from paper_1401_7457_gb300 import binding
+    codes, lens, ref = genome_reads
+    N = int(lens.sum()) + lens.size
+    with binding.Context(device=0, prefix_len=12, plan_flags=flags,
+                         budget_bytes=budget_for(N, 3, 8 if flags & 1 else 4)) as c:
+        assert_same(gpu_bwt(c, codes, lens, want_sa=True), ref, sa=True)
+        assert c.stats()["slices"] >= 2
+
