@@ -112,6 +112,12 @@ typedef struct {
  *                read into L2 ahead of the CTAs that sort them (by default
  *                they do when their arrays are 16-byte aligned). */
 #define CXBWT_PLAN_NO_PREFETCH 16
+/*  DIGIT_LISTING - list the suffixes of a build in slices with the general
+ *                digit pass (digit = slice and suffix length, ranked by warp
+ *                ballots) instead of the listing kernel whose threads each
+ *                own one suffix length (reads of one length of at most 255
+ *                bases). */
+#define CXBWT_PLAN_DIGIT_LISTING 32
 /* Test hook for failure handling: in the first digit pass of a build, tile 0
  * does not publish its counts, so tile 1's look-back wait runs out (after
  * wait_limit_ms).  The build then returns CXBWT_ETIMEOUT with unspecified

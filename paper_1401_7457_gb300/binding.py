@@ -335,6 +335,7 @@ class Context:
 
     ALGO_AUTO, ALGO_LSD, ALGO_GROUPS = 0, 1, 2
     PLAN_ID64, PLAN_READ_MAJOR, PLAN_TEST_STALL, PLAN_CARRY_BASE, PLAN_NO_PREFETCH = 1, 2, 4, 8, 16
+    PLAN_DIGIT_LISTING = 32
 
     def __init__(self, device: int = 0, budget_bytes: int = 0, async_: bool = False, timing: bool = False,
                  tile_items: int = 0, algorithm: int = 0, plan_flags: int = 0, batch_workers: int = 0,

@@ -39,6 +39,23 @@ thread_local std::string g_create_error;
 namespace cxbwt {
 namespace host {
 
+// The listing kernel (k_list.cu) lists a build's slices: reads of one length
+// of at most 255 bases, unless the plan flags ask for the digit pass.
+static bool list_kernel(const cxbwt_ctx* c, const Plan& pl) {
+  return pl.uniform && pl.Lmax <= 255 && !(c->opt.plan_flags & CXBWT_PLAN_DIGIT_LISTING);
+}
+
+// Tiles of the pass with the most of them: the generating digit passes
+// (every suffix, TILE per tile) or the listing kernel (whole reads per tile).
+static uint64_t status_tiles(const cxbwt_ctx* c, const Plan& pl, uint32_t TILE) {
+  uint64_t t = (pl.N + TILE - 1) / TILE;
+  if (list_kernel(c, pl)) {
+    const uint64_t rpt = list_reads_per_tile(pl.Lmax);
+    t = std::max<uint64_t>(t, (pl.n + rpt - 1) / rpt);
+  }
+  return t;
+}
+
 // Sort the slice's suffixes into r.vals[cur]; returns cur (0 or 1) through
 // *cur_out.  tev (or nullptr): events recorded before the digit passes and
 // after them.
@@ -149,6 +166,36 @@ int sort_slice(cxbwt_ctx* c, Run& r, const Slice& sl, int* cur_out, cudaEvent_t*
       ++r.sort_launches;
       r.sort_items += sl.rows;
     }
+  } else if (r.read_major && !sl.pregen && list_kernel(c, pl)) {
+    // Read-major listing of the slice's suffixes (the store read in address
+    // order), ordered by suffix length, window 0 carried: the listing kernel
+    // with one key range.
+    ListArgs la{};
+    la.R = r.R;
+    la.n_reads = uint32_t(pl.n);
+    la.reads_per_tile = list_reads_per_tile(pl.Lmax);
+    la.n_tiles = uint32_t((pl.n + la.reads_per_tile - 1) / la.reads_per_tile);
+    la.stage_rows = la.reads_per_tile * (pl.Lmax + 1);
+    la.n_slices = 1;
+    la.key_lo[0] = sl.key_lo;
+    la.key_last[0] = a.key_last;
+    la.vals[0] = r.vals[cur ^ 1];
+    la.keys[0] = r.keys[kin];
+    la.rows[0] = sl.rows;
+    la.digit_base = r.base;  // row 0: suffix length
+    la.status = a.status;
+    la.tile_counter = a.tile_counter;
+    la.err = a.err;
+    la.epoch = ++c->epoch;
+    la.timeout_ns = a.timeout_ns;
+    la.prefetch = a.prefetch;
+    if (tev) CX_TRY(pass_event_begin(c, r));
+    CX_CUDA(c, launch_list(la, idb, st));
+    if (tev) CX_TRY(pass_event_end(c, r, 0));
+    cur ^= 1;
+    ++r.sort_launches;
+    r.sort_items += sl.rows;
+    first = false;
   } else if (r.read_major && !sl.pregen) {
     // Read-major generated order (the store is read in address order),
     // filtered to the slice, stably sorted by suffix length, window 0 carried.
@@ -323,6 +370,36 @@ int split_pass(cxbwt_ctx* c, Run& r, const std::vector<Slice>& slices, const std
   uint32_t* d_sbase = r.base + size_t(std::max<uint32_t>(pl.D + pl.len_passes, 5)) * kRadix;
   uint8_t* d_split = reinterpret_cast<uint8_t*>(d_sbase + kRadix);
   CX_CUDA(c, cudaMemcpyAsync(d_sbase, sbase.data(), kRadix * 4, cudaMemcpyHostToDevice, r.st));
+  if (list_kernel(c, pl)) {
+    ListArgs la{};
+    la.R = r.R;
+    la.n_reads = uint32_t(pl.n);
+    la.reads_per_tile = list_reads_per_tile(L);
+    la.n_tiles = uint32_t((pl.n + la.reads_per_tile - 1) / la.reads_per_tile);
+    la.stage_rows = la.reads_per_tile * L1;
+    la.n_slices = S;
+    for (uint32_t si = 0; si < S; ++si) {
+      la.key_lo[si] = slices[si].key_lo;
+      la.key_last[si] = uint32_t(slices[si].key_hi - 1 - slices[si].key_lo);
+      la.vals[si] = vptr(c->vals[0].p, pl.idb, slices[si].arr0);
+      la.keys[si] = static_cast<uint32_t*>(c->keys[0].p) + slices[si].arr0;
+      la.rows[si] = slices[si].rows;
+    }
+    la.digit_base = d_sbase;
+    la.status = static_cast<unsigned long long*>(c->status.p);
+    la.tile_counter = r.d_counter;
+    la.err = r.d_err;
+    la.epoch = ++c->epoch;
+    la.timeout_ns = c->opt.wait_limit_ms > 0 ? uint64_t(c->opt.wait_limit_ms) * 1000000ull : kTimeoutNs;
+    la.prefetch = (c->opt.plan_flags & CXBWT_PLAN_NO_PREFETCH) ? 0u : 1u;
+    if (timing) CX_TRY(pass_event_begin(c, r));
+    CX_CUDA(c, launch_list(la, pl.idb, r.st));
+    if (timing) CX_TRY(pass_event_end(c, r, 2));
+    ++r.sort_launches;
+    r.sort_items += pl.N;
+    r.read_major = true;
+    return CXBWT_OK;
+  }
   CX_CUDA(c, cudaMemcpyAsync(d_split, split_of.data(), kRadix, cudaMemcpyHostToDevice, r.st));
   const uint32_t TILE = uint32_t(r.shape.tile());
   PassArgs a{};
@@ -522,7 +599,7 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
   // The look-back words cover every tile of a generated enumeration of all N
   // suffixes, so they are a fixed cost, not a per-row one.
   const double per_row = 2.0 * pl.idb + 8.0 + 8.0 / 33 + (out_sa && !sa_dev ? 8.0 : 0.0);
-  const uint64_t status_bytes = (pl.N + TILE - 1) / TILE * kRadix * 8;
+  const uint64_t status_bytes = status_tiles(c, pl, TILE) * kRadix * 8;
   const uint64_t fixed = uint64_t(pl.Lmax) * kRadix * 4 + uint64_t(pl.D + pl.len_passes + 5) * kRadix * 4 +
                          uint64_t(pl.W) * 4 * kRadix * 4 + (uint64_t(1) << kBucketBits) * 8 + status_bytes + (1u << 20);
   // Buffers sized per slice are reused (or regrown) by this build: they do
@@ -719,7 +796,7 @@ int build_impl(cxbwt_ctx* c, const uint32_t* reads, uint64_t n, const uint32_t* 
 
   uint32_t max_rows = 0;
   for (const Slice& sl : slices) max_rows = std::max(max_rows, sl.rows);
-  const uint64_t gen_tiles = (pl.N + TILE - 1) / TILE;
+  const uint64_t gen_tiles = status_tiles(c, pl, TILE);  // look-back words: the most tiles any pass has
 
   // A build in a few slices of 4-base buckets lists every slice in one
   // generating pass (kSrcInitSplit: digit = (slice, suffix length)) into its

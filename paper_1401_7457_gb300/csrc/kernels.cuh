@@ -77,6 +77,34 @@ struct PassArgs {
   uint32_t split_rows[kMaxSplit];
 };
 
+// The listing pass of a build in slices (k_list.cu): suffixes of reads of
+// one length L, enumerated read by read, kept when their first window lies
+// in one of n_slices key ranges, written to their slice's arrays in
+// (suffix length, read) order.  Digit d = s * (L + 1) + suffix length.
+constexpr uint32_t kListMaxStage = 4096;  // rows one tile stages in shared memory
+struct ListArgs {
+  ReadIndex R;                  // reads of one length (R.uniform_len = L, at most 255)
+  uint32_t n_reads;
+  uint32_t reads_per_tile;      // list_reads_per_tile(L)
+  uint32_t n_tiles;             // ceil(n_reads / reads_per_tile)
+  uint32_t stage_rows;          // reads_per_tile * (L + 1), at most kListMaxStage
+  uint32_t n_slices;            // S in 1 .. kMaxSplit, with S * (L + 1) <= 256
+  uint32_t key_lo[kMaxSplit];   // slice s keeps the suffixes whose first window w has
+  uint32_t key_last[kMaxSplit]; //   w - key_lo[s] <= key_last[s] (ranges do not overlap)
+  void* vals[kMaxSplit];        // slice s's ids (uint32 or uint64) and first windows, rows from 0
+  uint32_t* keys[kMaxSplit];
+  uint32_t rows[kMaxSplit];     // rows of slice s (writes beyond are refused: kErrBounds)
+  const uint32_t* digit_base;   // [S * (L + 1)]: row, in its slice, of the first suffix of digit d
+  unsigned long long* status;   // look-back words, [n_tiles * 256]
+  uint32_t* tile_counter;       // zero on entry; the kernel leaves it zero
+  uint32_t* err;                // device error word
+  uint32_t epoch;               // look-back flags of this pass: 2*epoch, 2*epoch+1
+  uint64_t timeout_ns;          // look-back wait limit
+  uint32_t prefetch;            // host: nonzero asks for the store words of later tiles to be read into L2
+};
+uint32_t list_reads_per_tile(uint32_t read_len);
+cudaError_t launch_list(const ListArgs& a, int id_bytes, cudaStream_t st);
+
 // Tile geometry of the digit pass (threads x items per thread).
 struct TileShape {
   int threads;

@@ -191,3 +191,43 @@ def test_group_depth_12_in_slices(genome_reads, flags):
         assert_same(gpu_bwt(c, codes, lens, want_sa=True), ref, sa=True)
         assert c.stats()["slices"] >= 2
 
+
+@pytest.mark.parametrize("length,n", [(20, 100_000), (60, 40_000), (100, 20_000)])
+@pytest.mark.parametrize("flags", [0, 1 | 8, 32])
+def test_listing_kernel_split(length, n, flags):
+    """Two slices listed by one pass of the listing kernel (each thread owns
+    one suffix length of every read of its tile: 195, 67 or 40 reads per
+    tile) or, with plan flag 32, of the general digit pass; 32-bit ids, and
+    64-bit ids carrying the preceding base: the oracle's result."""
+    _need_gpu()
+    from paper_1401_7457_gb300 import binding
+    g = synth.random_genome(n * length // 20, 130 + length)
+    codes, lens = synth.sample_reads(g, n, length, 131 + length, 0.01)
+    ref = oracle_of(codes, lens)
+    N = int(lens.sum()) + lens.size
+    with binding.Context(device=0, budget_bytes=split_budget(N, 8 if flags & 1 else 4), plan_flags=flags) as c:
+        got = gpu_bwt(c, codes, lens, want_sa=True)
+        st = c.stats()
+    assert_same(got, ref, sa=True)
+    assert st["slices"] == 2 and st["sort_pass_launches"] == 9, st
+
+
+@pytest.mark.parametrize("length,n", [(20, 100_000), (100, 20_000), (150, 12_000), (255, 6_000)])
+@pytest.mark.parametrize("flags", [2, 2 | 1 | 8, 2 | 32])
+def test_listing_kernel_per_slice(length, n, flags):
+    """About four slices, each listed by its own read-major pass over every
+    suffix that keeps the slice's key range (plan flag 2 takes the read-major
+    listing although the store fits L2): the listing kernel with one key
+    range (128 threads up to 127 bases, 256 above) or the digit pass (flag
+    32); the oracle's result."""
+    _need_gpu()
+    from paper_1401_7457_gb300 import binding
+    g = synth.random_genome(n * length // 20, 140 + length)
+    codes, lens = synth.sample_reads(g, n, length, 141 + length, 0.01)
+    ref = oracle_of(codes, lens)
+    N = int(lens.sum()) + lens.size
+    with binding.Context(device=0, budget_bytes=budget_for(N, 4, 8 if flags & 1 else 4), plan_flags=flags) as c:
+        got = gpu_bwt(c, codes, lens, want_sa=True)
+        st = c.stats()
+    assert_same(got, ref, sa=True)
+    assert st["slices"] >= 3, st
