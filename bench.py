@@ -63,19 +63,25 @@ WORKLOADS = {
 SAMPLE_CHUNK = 1 << 17
 
 
-def load_workload(name, rank=0, n_reads=0):
-    """(description, codes, lens) of a workload; rank > 0 draws an independent collection of the same shape."""
+def load_workload(name, rank=0, n_reads=0, genome_bp=0):
+    """(description, codes, lens) of a workload; rank > 0 draws an independent collection of the same shape.
+    genome_bp > 0 replaces the genome size of the genome-like and repeat-rich workloads (a smaller copy
+    of a workload at its own coverage, for profiling captures)."""
     from paper_1401_7457_gb300 import synth
+    desc = WORKLOADS[name]
     if name == "genome-like":
         seed = 2 if rank == 0 else synth.derive_seed(2, rank)
-        codes, lens = synth.genome_like(seed=seed, n_reads=n_reads or 1_000_000)
+        codes, lens = synth.genome_like(seed=seed, n_reads=n_reads or 1_000_000, genome_size=genome_bp or 5_000_000)
     elif name == "repeat-rich":
         seed = 3 if rank == 0 else synth.derive_seed(3, rank)
-        codes, lens = synth.repeat_rich(seed=seed, n_reads=n_reads or 50_000_000)
+        codes, lens = synth.repeat_rich(seed=seed, n_reads=n_reads or 50_000_000,
+                                        genome_size=genome_bp or 100_000_000)
     else:
         seed = 1 if rank == 0 else synth.derive_seed(1, rank)
         codes, lens = synth.uniform_reads(n_reads or 10_000, 100, seed)
-    return WORKLOADS[name], codes, lens
+    if genome_bp and name in ("genome-like", "repeat-rich"):
+        desc = desc.replace("5 Mbp" if name == "genome-like" else "100 Mbp", f"{genome_bp / 1e6:g} Mbp")
+    return desc, codes, lens
 
 
 # ncu summaries of the carried-key digit pass, by suffix id width.
@@ -861,6 +867,9 @@ def main():
     ap.add_argument("--no-config2", action="store_true", help="skip the genome-like measurement (config2 key)")
     ap.add_argument("--reads", type=int, default=0,
                     help="reads per GPU (0: the workload's own size; smaller only for profiling captures)")
+    ap.add_argument("--genome-mbp", type=float, default=0.0,
+                    help="genome size of the genome-like / repeat-rich workload in Mbp (0: its own; with --reads, "
+                         "a smaller copy at the workload's coverage for profiling captures)")
     ap.add_argument("--shard-workload", default="repeat-rich", choices=sorted(WORKLOADS),
                     help="the collection --workload sharded splits across the ranks")
     ap.add_argument("--workload", default="repeat-rich",
@@ -904,7 +913,7 @@ def main():
     args.warmup = max(args.warmup, 3)  # at least three untimed warm-up builds
 
     # Each rank builds its own independent collection (weak scaling, no data-path collective).
-    desc, codes, lens = load_workload(args.workload, rank, args.reads)
+    desc, codes, lens = load_workload(args.workload, rank, args.reads, int(args.genome_mbp * 1e6))
     res = measure(args, dist, world, local, dev, desc, codes, lens, args.steps, e2e_steps=max(3, min(args.steps, 10)))
 
     cpu = None

@@ -214,6 +214,39 @@ def test_plans_identical(case, algorithm):
         assert_same(gpu_bwt(c, codes, lens, want_sa=True), ref, sa=True)
 
 
+COVERAGE_CASES = ["genome_50x", "repeats_50x", "a_rich_50x", "reads_36_50x", "reads_150_50x", "reads_300_50x"]
+
+
+def coverage_case(case):
+    """Collections whose groups of equal first 16 bases are as large and as
+    structured as the benchmark's: reads at 50x coverage (about 21 suffixes
+    of one locus per strand, ordered by length, with 1% substitutions), 1 kb
+    repeats, an A-rich genome (long A runs: many rows whose A-padded keys are
+    equal), and read lengths from 36 to 300 bases (2 to 24 key words)."""
+    if case == "genome_50x":
+        return synth.sample_reads(synth.random_genome(40_000, 61), 20_000, 100, 62, 0.01)
+    if case == "repeats_50x":
+        return synth.repeat_rich(seed=63, n_reads=40_000, genome_size=80_000)
+    if case == "a_rich_50x":
+        g = np.random.default_rng(64).choice(4, size=40_000, p=[0.7, 0.1, 0.1, 0.1]).astype(np.uint8)
+        return synth.sample_reads(g, 20_000, 100, 65, 0.01)
+    length = int(case.split("_")[1])
+    return synth.sample_reads(synth.random_genome(length * 400, 66), 20_000, length, 67, 0.01)
+
+
+@pytest.mark.parametrize("case", COVERAGE_CASES)
+def test_group_finish_at_high_coverage(case):
+    """The group plan on groups of benchmark size and shape (warp windows of
+    several 20-row groups, ties of equal A-padded keys, 2 to 24 key words):
+    the oracle's result, suffix order included."""
+    from paper_1401_7457_gb300 import binding
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    codes, lens = coverage_case(case)
+    with binding.Context(device=0, algorithm=2) as c:
+        assert_same(gpu_bwt(c, codes, lens, want_sa=True), oracle_of(codes, lens), sa=True)
+
+
 @pytest.mark.parametrize("case", PLAN_CASES)
 def test_group_plan_depth_12(case):
     """The group plan with l = 12 (prefix_len): three LSD passes sort the
