@@ -143,3 +143,21 @@ def test_summarize_clocks():
     s = bench.summarize_clocks(rows, "x")
     assert s == {"sm_mhz": 2000.0, "sm_max_mhz": 2070.0, "samples": 3, "reasons": ["sw_power_cap"], "source": "x"}
     assert bench.summarize_clocks([], "x") is None
+
+
+def test_smaller_copy_of_a_workload_keeps_its_coverage():
+    """--genome-mbp with --reads draws a smaller copy of a workload at the
+    coverage the reads give (for profiling captures); the description names
+    the genome it was drawn from, and the default draw is unchanged."""
+    import bench
+    from paper_1401_7457_gb300 import synth
+    desc, codes, lens = bench.load_workload("repeat-rich", 0, 4000, 8_000)
+    assert "8000 Mbp" not in desc and "0.008 Mbp" in desc and "100 Mbp" not in desc
+    assert lens.size == 4000 and int(lens.sum()) == codes.size == 400_000
+    want_codes, want_lens = synth.repeat_rich(seed=3, n_reads=4000, genome_size=8_000)
+    assert (codes == want_codes).all() and (lens == want_lens).all()
+    desc0, codes0, _ = bench.load_workload("repeat-rich", 0, 4000)
+    assert desc0 == bench.WORKLOADS["repeat-rich"]
+    assert (codes0 == synth.repeat_rich(seed=3, n_reads=4000)[0]).all()
+    desc_gl, _, lens_gl = bench.load_workload("genome-like", 0, 2000, 20_000)
+    assert "0.02 Mbp" in desc_gl and lens_gl.size == 2000
